@@ -1,0 +1,234 @@
+"""FP64 pins for the oracle: dense Cholesky, textbook CG facts, the rounding
+error invariants of Section 3, the model problem row of Table 2, and a
+library cross-check against scipy's CG."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import oracle as O
+import problems as P
+
+EPS = 2.0 ** -53
+
+
+def _poisson_sp(dims):
+    rp, ci, v = P.poisson_csr(dims)
+    n = len(rp) - 1
+    return sp.csr_matrix((v, ci, rp), shape=(n, n))
+
+
+def _spd_with_cond(n, kappa, seed):
+    rng = np.random.default_rng(seed)
+    Q = P.haar_orthogonal(n, rng)
+    lam = np.geomspace(1.0, kappa, n)
+    return (Q * lam) @ Q.T, rng
+
+
+@pytest.mark.parametrize("variant", O.VARIANTS)
+@pytest.mark.parametrize("precond", [False, True])
+def test_solution_matches_cholesky(variant, precond):
+    for A, b in [
+        (_poisson_sp((10, 10)).toarray(), np.random.default_rng(1).uniform(-1, 1, 100)),
+        (P.model_problem(48, 0.8, 1e3).A, P.model_problem(48, 0.8, 1e3).b),
+        (_spd_with_cond(200, 1e3, 4)[0], np.random.default_rng(5).standard_normal(200)),
+    ]:
+        A = 0.5 * (A + A.T)
+        xc = sla.cho_solve(sla.cho_factor(A), b)
+        d = O.jacobi_inverse_diagonal(A) if precond else None
+        # GV-CG cannot reach 1e-12 on the model problem (Table 2: min error 1e-10)
+        tol = 1e-8 if variant == "gv" else 1e-12
+        res = O.solve(variant, A, b, d=d, tol=tol, maxit=10 * len(b))
+        assert res.status == O.OK, (variant, res.status)
+        kappa = np.linalg.cond(A)
+        err = np.linalg.norm(res.x - xc) / np.linalg.norm(xc)
+        assert err <= 10 * tol * kappa, (variant, err)
+
+
+def test_hs_a_norm_error_monotone_before_stagnation():
+    A = _poisson_sp((12, 12))
+    rng = np.random.default_rng(2)
+    xs = rng.uniform(-1, 1, 144)
+    b = A @ xs
+    res = O.hs_cg(A, b, tol=1e-10, maxit=500, record=500)
+    errs = [O.a_norm_error(A, xs, x) for x, _ in res.iterates]
+    e0 = errs[0]
+    for k in range(1, len(errs)):
+        if errs[k] < 1e-9 * e0:
+            break
+        assert errs[k] <= errs[k - 1] * (1 + 1e-12), k
+
+
+@pytest.mark.parametrize("precond", [False, True])
+def test_variants_agree_with_hs_first_10_iterations(precond):
+    A, rng = _spd_with_cond(60, 50.0, 7)
+    b = rng.standard_normal(60)
+    d = O.jacobi_inverse_diagonal(A) if precond else None
+    ref = O.hs_cg(A, b, d=d, maxit=10, record=10)
+    for v in O.VARIANTS:
+        res = O.solve(v, A, b, d=d, maxit=10, record=10)
+        assert len(res.iterates) == 11
+        for (xa, ra), (xb, rb) in zip(ref.iterates[1:], res.iterates[1:]):
+            assert np.linalg.norm(xa - xb) <= 1e-12 * np.linalg.norm(xa), v
+            assert np.linalg.norm(ra - rb) <= 1e-12 * np.linalg.norm(b), v
+
+
+def _nu_gap_worst(res, b, n):
+    """max_k |<r_k,r_k> - nu'_k| / (eps (30 + 7n)(||r_{k-1}||^2 + ||r_k||^2)) (Eq. 3.16)."""
+    prev = float(np.dot(b, b))
+    worst = 0.0
+    for _, (nu_pred, rr) in res.extra["nu_gap"]:
+        bound = EPS * (30 + 7 * n) * (prev + rr)
+        worst = max(worst, abs(rr - nu_pred) / bound)
+        prev = rr
+    return worst
+
+
+@pytest.mark.parametrize("variant", ["pr", "pipe_pr"])
+def test_nu_prime_gap_bound(variant):
+    """Section 3.1, Eq. 3.16: the nu'-gap stays within local rounding errors."""
+    prob = P.model_problem(48, 0.8, 1e3)
+    res = O.solve(variant, prob.A, prob.b, maxit=150, track=("nu_gap",))
+    assert len(res.extra["nu_gap"]) == 150
+    assert _nu_gap_worst(res, prob.b, 48) <= 1.0
+    A = _poisson_sp((16, 16))
+    b = np.random.default_rng(9).uniform(-1, 1, 256)
+    res = O.solve(variant, A, b, maxit=200, track=("nu_gap",))
+    assert _nu_gap_worst(res, b, 256) <= 1.0
+
+
+def test_nu_prime_gap_without_recompute_grows():
+    """Eq. 3.17-3.18: carrying nu' from nu'_{k-1} accumulates the gap."""
+    prob = P.model_problem(48, 0.8, 1e3)
+    res = O.pr_cg(prob.A, prob.b, maxit=150, recompute_nu=False, track=("nu_gap",))
+    assert _nu_gap_worst(res, prob.b, 48) > 1e3
+
+
+def _w_gap_ratios(res, A):
+    """||A r_k - w'_k|| / (eps c ||A|| (||r_{k-1}|| + ||r_k||)) with c = m sqrt(n) (Eq. 3.4)."""
+    n = A.shape[0]
+    c = n * np.sqrt(n)
+    An = np.linalg.norm(A, 2)
+    out = []
+    prev = None
+    for _, (rk, wp) in res.extra["w_gap"]:
+        nr = np.linalg.norm(rk)
+        prev = nr if prev is None else prev
+        out.append(np.linalg.norm(A @ rk - wp) / (EPS * c * An * (nr + prev)))
+        prev = nr
+    return np.array(out)
+
+
+def test_pipe_w_gap_resets_each_iteration():
+    """Eq. 3.22: with w recomputed the w'-gap is a sum of local rounding errors;
+    Eq. 3.23: without it the gap accumulates (Fig. 2)."""
+    prob = P.model_problem(48, 0.8, 1e3)
+    res = O.pipe_pr_cg(prob.A, prob.b, maxit=120, track=("w_gap",))
+    ratios = _w_gap_ratios(res, prob.A)
+    assert len(ratios) == 120 and ratios.max() <= 1.0
+    res = O.pipe_pr_cg(prob.A, prob.b, maxit=120, recompute_w=False, track=("w_gap",))
+    ratios = _w_gap_ratios(res, prob.A)
+    assert ratios.max() > 10.0
+    assert ratios[-1] > 100 * ratios[:5].max()
+
+
+def test_no_recompute_pr_stalls_near_sqrt_eps():
+    """Section 3.1 (after Eq. 3.18) and Fig. 1: without recompute nu' can no
+    longer be trusted once ||r_k|| ~ sqrt(eps); with it PR-CG goes far below."""
+    prob = P.model_problem(48, 0.8, 1e3)
+    bad = O.pr_cg(prob.A, prob.b, maxit=300, recompute_nu=False)
+    good = O.pr_cg(prob.A, prob.b, maxit=300)
+    assert min(bad.hist) > 1e-10
+    assert min(good.hist) < 1e-14
+    # for some eigenvector draws nu' turns negative and the run breaks down
+    prob5 = P.model_problem(48, 0.8, 1e3, rng=np.random.default_rng(5))
+    res = O.pr_cg(prob5.A, prob5.b, maxit=300, recompute_nu=False)
+    assert res.status == O.BREAKDOWN and 1e-9 < res.hist[-1] < 1e-6
+    assert O.pr_cg(prob5.A, prob5.b, maxit=300).status == O.NOT_CONVERGED
+
+
+def _table2_stats(variant, prob, d=None, its=200):
+    res = O.solve(variant, prob.A, prob.b, d=d, maxit=its, record=its)
+    e0 = O.a_norm_error(prob.A, prob.x_star, np.zeros_like(prob.b))
+    errs = np.array([O.a_norm_error(prob.A, prob.x_star, x) / e0 for x, _ in res.iterates])
+    k5 = int(np.argmax(errs < 1e-5))
+    return k5, float(np.log10(errs.min()))
+
+
+# Table 2, row model_48_8_3 (no preconditioner, then Jacobi):
+# iterations to a 1e5 reduction of the A-norm error and min log10 error.
+TABLE2_NONE = {"hs": (43, -14.32), "cgcg": (42, -14.28), "m": (45, -14.31), "pr": (44, -14.32),
+               "gv": (45, -10.23), "pipe_m": (43, -13.67), "pipe_pr": (44, -13.66)}
+TABLE2_JAC = {"hs": (49, -14.30), "cgcg": (48, -14.25), "m": (50, -14.28), "pr": (50, -14.29),
+              "gv": (52, -10.66), "pipe_m": (50, -13.70), "pipe_pr": (50, -13.72)}
+
+
+@pytest.mark.parametrize("variant", O.VARIANTS)
+def test_model_48_8_3_table2_soft_pin(variant):
+    """Soft pin: the paper's eigenvector draw is unknown, so iteration counts get
+    +-3 (unpreconditioned: the spectrum is fixed by Eq. 4.1) or +-5 (Jacobi:
+    diag(A) depends on the draw) and the minimum error +-0.5 decades."""
+    prob = P.model_problem(48, 0.8, 1e3)
+    k5, emin = _table2_stats(variant, prob)
+    ref_k, ref_e = TABLE2_NONE[variant]
+    assert abs(k5 - ref_k) <= 3 and abs(emin - ref_e) <= 0.5, (k5, emin)
+    k5, emin = _table2_stats(variant, prob, O.jacobi_inverse_diagonal(prob.A))
+    ref_k, ref_e = TABLE2_JAC[variant]
+    assert abs(k5 - ref_k) <= 5 and abs(emin - ref_e) <= 0.5, (k5, emin)
+
+
+def test_gv_loses_accuracy_pipe_pr_does_not():
+    """Table 2: GV-CG's attainable accuracy is orders of magnitude worse; pipe-PR-CG
+    stays within ~1 decade of HS-CG."""
+    prob = P.model_problem(48, 0.8, 1e3)
+    _, e_hs = _table2_stats("hs", prob)
+    _, e_gv = _table2_stats("gv", prob)
+    _, e_ppr = _table2_stats("pipe_pr", prob)
+    assert e_gv > e_hs + 3
+    assert e_ppr < e_hs + 1
+
+
+def test_hs_iteration_count_matches_scipy_cg():
+    A = _poisson_sp((32, 32))
+    b = np.random.default_rng(11).uniform(-1, 1, 1024)
+    count = [0]
+
+    def cb(_):
+        count[0] += 1
+
+    x, info = spla.cg(A, b, rtol=1e-10, atol=0.0, maxiter=5000, callback=cb)
+    assert info == 0
+    res = O.hs_cg(A, b, tol=1e-10, maxit=5000)
+    assert res.status == O.OK
+    assert abs(res.iters - count[0]) <= max(2, 0.02 * count[0])
+    assert np.linalg.norm(res.x - x) <= 1e-8 * np.linalg.norm(x)
+
+
+def test_statuses():
+    A = _poisson_sp((8, 8))
+    b = np.ones(64)
+    for v in O.VARIANTS:
+        res = O.solve(v, A, b, tol=1e-30, maxit=7)
+        assert res.status == O.NOT_CONVERGED and res.iters == 7 and len(res.hist) == 8
+        res = O.solve(v, A, np.zeros(64), tol=1e-10)
+        assert res.status == O.OK and res.iters == 0 and not res.x.any()
+    # an indefinite matrix: mu <= 0 or nu' < 0 ends the run with BREAKDOWN
+    Ai = np.diag([1.0, 2.0, -3.0, 4.0])
+    bi = np.ones(4)
+    for v in O.VARIANTS:
+        res = O.solve(v, Ai, bi, tol=1e-12, maxit=20)
+        assert res.status == O.BREAKDOWN, v
+
+
+def test_jacobi_reduces_iterations_on_varcoef():
+    prob = P.grid_problem((16, 16), "t_vc", sigma=2.0)
+    rp, ci, v = prob.csr
+    A = sp.csr_matrix((v, ci, rp), shape=(256, 256))
+    d = O.jacobi_inverse_diagonal(A)
+    for var in ("hs", "pr", "pipe_pr"):
+        none = O.solve(var, A, prob.b, tol=1e-10, maxit=5000)
+        jac = O.solve(var, A, prob.b, d=d, tol=1e-10, maxit=5000)
+        assert none.status == O.OK and jac.status == O.OK
+        assert jac.iters < none.iters
+        assert O.true_relres(A, prob.b, jac.x) < 1e-9
