@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark: PR-CG vs HS-CG iterations/s and HBM GB/s on one GB300.
+
+Default workload (the 3D configuration of the method's targets): 3D 7-point
+Poisson on a 256^3 grid (n = 16,777,216, nnz = 117,047,296), FP64, CSR,
+Jacobi preconditioner, x_true ~ U(-1, 1), b = A x_true, x_0 = 0, solved by
+PR-CG to ||r_k|| / ||b|| <= 1e-10.  One step = one complete solve
+(initialisation, iterations, device-side loop control) on resident inputs;
+value = iterations / device time.  HS-CG, pipe-PR-CG, the matrix-free
+stencil and the 128^3 log-normal diffusion system are reported beside it.
+
+--impl reference times the CPU oracle (plain numpy / scipy, one thread) on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import os
+
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse  # noqa: E402
+import hashlib  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG iters/s & HBM GB/s (PR vs HS-CG, FP64, 256^3); batched solves/s @1e-8"
+L2_BYTES = 129e6
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- bytes model
+def model_bytes(variant: str, op: str, precond: str, n: int, nnz: int, dim: int = 3) -> float:
+    """Algorithmic DRAM bytes of one iteration (all sweeps of it).
+
+    V = 8n bytes per vector sweep.  A = 12 nnz + 4 (n+1) for CSR, 0 for the
+    constant stencil, ~(dim + 1) V for the variable-coefficient stencil (face
+    arrays + diagonal).  Sweeps read / write:
+      HS:   A: R x p r s  W x r      B: R r p  W p s  (+A)       -> 10V + A
+      PR:   R x p r s  W x r p s (+A)                              ->  8V + A
+      pipe: R x p r s w u  W x r p s w u (+A, one pass)            -> 12V + A
+    Jacobi adds r~ (PR, pipe) and s~ (pipe) read+write, and one read of d per
+    sweep when d is a vector (CSR, variable coefficients).
+    """
+    V = 8.0 * n
+    if op == "csr":
+        A = 12.0 * nnz + 4.0 * (n + 1)
+    elif op == "varcoef":
+        A = (dim + 1) * V
+    else:
+        A = 0.0
+    dvec = precond == "jacobi" and op in ("csr", "varcoef")
+    jac = precond == "jacobi"
+    if variant == "hs":
+        return 10 * V + A + (2 * V if dvec else 0.0)
+    if variant in ("pr", "m"):
+        return 8 * V + A + (2 * V if jac else 0.0) + (V if dvec else 0.0)
+    if variant in ("pipe_pr", "pipe_m"):
+        return 12 * V + A + (4 * V if jac else 0.0) + (V if dvec else 0.0)
+    raise KeyError(variant)
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags)
+                          if f.lower() in ("active", "1")})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- workloads
+def build_problem(name: str):
+    import problems as P
+    if name.startswith("poisson3d_256"):
+        return P.poisson3d(256)
+    if name.startswith("poisson3d_"):
+        return P.poisson3d(int(name.split("_")[1]))
+    if name.startswith("varcoef3d_128"):
+        return P.varcoef3d(128)
+    raise KeyError(name)
+
+
+def make_solver(G, prob, op, precond):
+    if op == "csr":
+        rp, ci, v = prob.csr
+        return G.Solver.from_csr(rp, ci, v, precond=precond)
+    return G.Solver.from_stencil(prob.dims, face_coeff=prob.face_array(), diag_shift=prob.shift,
+                                 precond=precond)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1905_01549_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_tag: str):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, or
+    None if the kernel sources changed since it was captured."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            tab = json.load(f)
+    except Exception:
+        return None
+    ent = tab.get(kernel_tag)
+    if not ent or ent.get("source_sha") != kernel_source_hash():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def time_solves(S, b, variant, tol, maxit, steps, warmup):
+    """Device time of `steps` solves (after `warmup`), from the library's events."""
+    import torch
+    from paper_1905_01549_gb300 import binding
+    x = torch.zeros(S.n, dtype=torch.float64, device="cuda")
+    for _ in range(warmup):
+        x.zero_()
+        S.solve(b, x0=x, variant=variant, tol=tol, maxit=maxit)
+    torch.cuda.synchronize()
+    dev_ms, iters, launches = [], [], 0
+    res = None
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        x.zero_()
+        res = S.solve(b, x0=x, variant=variant, tol=tol, maxit=maxit)
+        dev_ms.append(res.init_ms + res.loop_ms)
+        iters.append(res.iters)
+        launches += binding.prcg_last_launches(S.handle)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    return dict(dev_ms=dev_ms, iters=iters, launches=launches, wall=wall, last=res,
+                loop_ms=res.loop_ms, status=res.status)
+
+
+def run_ours(args):
+    import torch
+    import paper_1905_01549_gb300 as G
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    wl = args.workload
+    prob = build_problem(wl)
+    n = prob.n
+    nnz = len(prob.csr[2]) if prob.csr is not None else 0
+    op, precond, variant, tol = "csr", "jacobi", "pr", 1e-10
+    maxit = 20000
+    b_dev = torch.from_numpy(prob.b).cuda()
+    S = make_solver(G, prob, op, precond)
+
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        main = time_solves(S, b_dev, variant, tol, maxit, args.steps, args.warmup)
+    torch.cuda.synchronize()
+    dev_s = sum(main["dev_ms"]) / 1e3
+    tot_iters = sum(main["iters"])
+    if dist is not None:
+        t = torch.tensor([dev_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        it = torch.tensor([float(tot_iters)], device="cuda")
+        dist.all_reduce(it, op=dist.ReduceOp.SUM)
+        dev_s_max, all_iters = float(t.item()), float(it.item())
+    else:
+        dev_s_max, all_iters = dev_s, float(tot_iters)
+    value = all_iters / dev_s_max
+    K = main["iters"][-1]
+    peak, peak_kind = _peaks()
+    bytes_it = model_bytes(variant, op, precond, n, nnz)
+    per_launch_s = main["loop_ms"] / 1e3 / max(K, 1)
+    achieved = bytes_it / per_launch_s / 1e9
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "iters/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": dev_s_max * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": wl, "n": n, "nnz": nnz, "operator": op, "precond": precond,
+                   "variant": variant, "tol": tol, "iters_per_solve": K,
+                   "step": "one complete solve to tol on resident inputs",
+                   "l2": "inputs larger than L2 (CSR %.2f GB + vectors)" % ((12 * nnz + 4 * n) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_kind,
+                     "kernel": "k_pr<CsrOp,PcVec>",
+                     "bytes_per_launch": bytes_it,
+                     "launch_us": per_launch_s * 1e6,
+                     "traffic": ncu_traffic("k_pr<CsrOp,PcVec>@poisson3d_256")},
+        "gpu_launches": main["launches"],
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_extras:
+        line["e2e"] = run_e2e(G, S, prob, variant, tol, maxit, args)
+        line["variants"] = run_variants(G, prob, S, b_dev, args)
+        if world == 1:
+            line["cpu_baseline"] = run_cpu_baseline(prob, variant, precond, args)
+    S.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(G, S, prob, variant, tol, maxit, args):
+    """Same metric through the C ABI with host (pinned) b and x: the
+    host->device copy of b and x_0 and the device->host copy of x_K are
+    inside each timed call."""
+    import torch
+    b_h = torch.from_numpy(prob.b).pin_memory()
+    x_h = torch.zeros(prob.n, dtype=torch.float64).pin_memory()
+    for _ in range(1):
+        x_h.zero_()
+        S.solve(b_h, x0=x_h, variant=variant, tol=tol, maxit=maxit)
+    tot, iters = 0.0, 0
+    for _ in range(max(2, args.steps // 2)):
+        x_h.zero_()
+        t0 = time.perf_counter()
+        r = S.solve(b_h, x0=x_h, variant=variant, tol=tol, maxit=maxit)
+        tot += time.perf_counter() - t0
+        iters += r.iters
+    return {"value": iters / tot, "unit": "iters/s", "h2d_bytes_per_step": 16 * prob.n,
+            "d2h_bytes_per_step": 8 * prob.n + 256,
+            "note": "prcg_solve with pinned host b, x; copies inside the timed call"}
+
+
+def run_variants(G, prob, S_main, b_dev, args):
+    """HS vs PR vs pipe-PR on CSR and the matrix-free stencil (same system),
+    and the 128^3 log-normal diffusion system."""
+    peak, _ = _peaks()
+    out = {}
+    n = prob.n
+    nnz = len(prob.csr[2])
+    tol, maxit = 1e-10, 20000
+    for op in ("csr", "stencil"):
+        S = S_main if op == "csr" else make_solver(G, prob, op, "jacobi")
+        for variant in ("hs", "pr", "pipe_pr"):
+            r = time_solves(S, b_dev, variant, tol, maxit, steps=2, warmup=1)
+            K = r["iters"][-1]
+            per = r["loop_ms"] / 1e3 / K
+            by = model_bytes(variant, op, "jacobi", n, nnz)
+            out[f"{op}/jacobi/{variant}"] = {
+                "iters_per_s": sum(r["iters"]) / (sum(r["dev_ms"]) / 1e3), "iters": K,
+                "us_per_iter": per * 1e6, "model_gb_per_iter": by / 1e9,
+                "achieved_gbs": by / per / 1e9, "frac": by / per / 1e9 / peak,
+                "status": r["status"]}
+        if op != "csr":
+            S.close()
+    # variable-coefficient diffusion 128^3, sigma = 2, Jacobi
+    import torch
+    vc = build_problem("varcoef3d_128")
+    bvc = torch.from_numpy(vc.b).cuda()
+    for op in ("csr", "varcoef"):
+        S = make_solver(G, vc, "csr" if op == "csr" else "stencil", "jacobi")
+        for variant in ("hs", "pr", "pipe_pr"):
+            r = time_solves(S, bvc, variant, tol, maxit, steps=2, warmup=1)
+            K = r["iters"][-1]
+            per = r["loop_ms"] / 1e3 / K
+            by = model_bytes(variant, op, "jacobi", vc.n, len(vc.csr[2]))
+            out[f"varcoef128_{op}/jacobi/{variant}"] = {
+                "iters_per_s": sum(r["iters"]) / (sum(r["dev_ms"]) / 1e3), "iters": K,
+                "us_per_iter": per * 1e6, "achieved_gbs": by / per / 1e9,
+                "frac_l2_note": "2M unknowns: vectors are 16.8 MB, partly L2-resident",
+                "status": r["status"]}
+        S.close()
+    return out
+
+
+def oracle_sample(prob, variant, precond, iters):
+    """Seconds of `iters` oracle iterations (init time subtracted)."""
+    import scipy.sparse as sp
+    import oracle as O
+    rp, ci, v = prob.csr
+    A = sp.csr_matrix((v, ci, rp), shape=(prob.n, prob.n))
+    d = O.jacobi_inverse_diagonal(A) if precond == "jacobi" else None
+    t0 = time.perf_counter()
+    O.solve(variant, A, prob.b, d=d, tol=0.0, maxit=0)
+    t_init = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    O.solve(variant, A, prob.b, d=d, tol=0.0, maxit=iters)
+    t_run = time.perf_counter() - t0
+    return max(t_run - t_init, 1e-9), t_run
+
+
+def run_cpu_baseline(prob, variant, precond, args):
+    iters = 6
+    t_loop, t_all = oracle_sample(prob, variant, precond, iters)
+    return {"value": iters / t_loop, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{iters} PR-CG iterations of the same 256^3 CSR Jacobi system "
+                      f"(numpy + scipy CSR matvec, one thread; initialisation timed "
+                      f"separately and subtracted; {t_all:.1f} s total)"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: each step is a bounded sample (3
+    iterations) of the same workload on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import scipy.sparse as sp
+    import oracle as O
+    prob = build_problem(args.workload)
+    rp, ci, v = prob.csr
+    A = sp.csr_matrix((v, ci, rp), shape=(prob.n, prob.n))
+    d = O.jacobi_inverse_diagonal(A)
+    per = 3
+    for _ in range(args.warmup):
+        O.pr_cg(A, prob.b, d=d, tol=0.0, maxit=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.pr_cg(A, prob.b, d=d, tol=0.0, maxit=per)
+    wall = time.perf_counter() - t0
+    value = per * args.steps / wall
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "n": prob.n, "nnz": len(v), "operator": "csr",
+                       "precond": "jacobi", "variant": "pr", "tol": 1e-10},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: oracle PR-CG initialisation + {per} iterations "
+                                       "(numpy + scipy, one thread)"},
+            "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="poisson3d_256_csr_jacobi_pr")
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import __graft_entry__
+    __graft_entry__.build()
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

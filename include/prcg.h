@@ -1,0 +1,162 @@
+/*
+ * prcg.h -- C ABI of the GB300 (sm_103a) predict-and-recompute CG library.
+ *
+ * The library solves A x = b for a symmetric positive definite A, optionally
+ * with a symmetric positive definite preconditioner M^{-1} (Section 1 of
+ * Chen & Carson, "Predict-and-recompute conjugate gradient variants": the
+ * methods need only products with A and M^{-1}).  The caller supplies A,
+ * the preconditioner choice, b and x_0 and nothing else (the variants take
+ * exactly the inputs of HS-CG, Section 1).
+ *
+ * Variants (one fused CUDA sweep per grid-wide reduction):
+ *   PRCG_HS       HS-CG, Algorithm 1 -- two reductions per iteration
+ *   PRCG_PR       PR-CG, Algorithm 2 -- nu'_k predicted by Eq. 2.3, nu_k
+ *                 recomputed with mu, sigma, gamma in one reduction
+ *   PRCG_PIPE_PR  pipe-PR-CG, Algorithm 3 -- s, s~ from the predicted w',
+ *                 u = A s~ and w = A r~ (recomputed) in one pass over A
+ *                 together with the four inner products
+ *   PRCG_M, PRCG_PIPE_M, PRCG_CGCG, PRCG_GV are the Appendix E variants.
+ *
+ * Threading: a context is not thread-safe; use one context per host thread.
+ * All work of a context runs on the CUDA stream given at creation (or the
+ * legacy default stream when NULL) and on one internal stream ordered after it.
+ *
+ * Pointers: every array argument may be a host pointer (pageable or pinned)
+ * or a device pointer of the current device; copies use unified addressing
+ * (cudaMemcpyDefault), which tells the two apart.  Nothing passed in is
+ * retained after the call returns; the caller keeps ownership.
+ *
+ * Return values: an int status, PRCG_OK (0) on success.  Negative values
+ * mean no result was produced; prcg_last_error() describes the failure.
+ */
+#ifndef PRCG_H
+#define PRCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct prcg_ctx prcg_ctx;
+
+enum prcg_variant {
+    PRCG_HS = 0,
+    PRCG_PR = 1,
+    PRCG_PIPE_PR = 2,
+    PRCG_M = 3,
+    PRCG_PIPE_M = 4,
+    PRCG_CGCG = 5,
+    PRCG_GV = 6
+};
+
+enum prcg_precond {
+    PRCG_PRECOND_NONE = 0,
+    PRCG_PRECOND_JACOBI = 1   /* M^{-1} = diag(1 / a_ii) (Section 4) */
+};
+
+enum prcg_status {
+    PRCG_OK = 0,               /* ||r_K|| / ||b|| <= tol                         */
+    PRCG_NOT_CONVERGED = 1,    /* K = maxit reached; x holds x_maxit            */
+    PRCG_BREAKDOWN = 2,        /* mu <= 0, nu <= 0, nu' < 0 or a non-finite
+                                  scalar (Section 3.1: the predicted nu' must
+                                  stay positive); x holds the last iterate    */
+    PRCG_ERR_INVALID = -1,     /* bad argument                                  */
+    PRCG_ERR_CUDA = -2,        /* a CUDA call failed                            */
+    PRCG_ERR_OOM = -3,         /* device allocation failed                      */
+    PRCG_ERR_TIMEOUT = -4,     /* the device loop ran more bodies than maxit
+                                  allows (internal safety limit)                */
+    PRCG_ERR_UNSUPPORTED = -5  /* variant / operator combination not built      */
+};
+
+/*
+ * prcg_create_csr -- context for a sparse matrix in CSR form.
+ *   n        number of rows = columns (1 <= n < 2^31)
+ *   nnz      number of stored entries (row_ptr[n] == nnz, nnz < 2^31)
+ *   row_ptr  int32[n + 1], non-decreasing, row_ptr[0] == 0
+ *   col_idx  int32[nnz], each in [0, n)
+ *   vals     double[nnz]
+ *   precond  prcg_precond; Jacobi needs every a_ii present and > 0
+ *   cuda_stream  cudaStream_t (void*) the context's work is ordered on
+ * The arrays are copied into context-owned device memory (the caller may
+ * free them afterwards).  Symmetry and definiteness are not checked up
+ * front: a non-SPD A shows up as PRCG_BREAKDOWN during prcg_solve.
+ * Returns PRCG_ERR_INVALID for inconsistent sizes or indices out of range.
+ */
+int prcg_create_csr(prcg_ctx** out, int64_t n, int64_t nnz,
+                    const int32_t* row_ptr, const int32_t* col_idx, const double* vals,
+                    int precond, void* cuda_stream);
+
+/*
+ * prcg_create_stencil -- matrix-free structured-grid operator, Dirichlet-0.
+ *   dim          2 (5-point) or 3 (7-point); nz is ignored (1) for dim 2
+ *   nx, ny, nz   grid sizes, lexicographic order with x fastest
+ *   face_coeff   NULL: constant-coefficient Poisson, diagonal 2*dim, off-
+ *                diagonal -1.  Otherwise one coefficient c_f > 0 per cell face
+ *                including boundary faces, concatenated as x-faces
+ *                [nz][ny][nx+1], y-faces [nz][ny+1][nx], (3D) z-faces
+ *                [nz+1][ny][nx]; A = sum_f c_f (e_a - e_b)(e_a - e_b)^T with
+ *                e_b = 0 on boundary faces.  Copied into the context.
+ *   diag_shift   added to the diagonal (>= 0 keeps A SPD)
+ *   precond      prcg_precond
+ * n = nx*ny*nz must be < 2^31.
+ */
+int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t nz,
+                        const double* face_coeff, double diag_shift, int precond,
+                        void* cuda_stream);
+
+/*
+ * prcg_solve -- run one variant from x_0 until ||r_k|| / ||b|| <= tol.
+ *   variant   prcg_variant
+ *   b         double[n] right-hand side (host or device)
+ *   x         double[n]; in: x_0, out: x_K (host or device)
+ *   tol       relative tolerance on the updated residual r_k (>= 0)
+ *   maxit     maximum number of iterations (>= 0)
+ *   residual_history  NULL or double[maxit + 1]; entries 0..K receive
+ *             ||r_k|| / ||b|| (updated residual), the rest are untouched
+ *   iters_out NULL or receives K, the number of completed iterations
+ *   final_true_relres_out NULL or receives ||b - A x_K|| / ||b||
+ * Returns PRCG_OK, PRCG_NOT_CONVERGED, PRCG_BREAKDOWN (x holds x_K in all
+ * three) or a negative error (x untouched).  If b == 0, x is set to 0 and
+ * K = 0.  The call blocks until the result is on the host.
+ */
+int prcg_solve(prcg_ctx* ctx, int variant, const double* b, double* x,
+               double tol, int maxit, double* residual_history,
+               int* iters_out, double* final_true_relres_out);
+
+/*
+ * prcg_last_timing -- device time of the last prcg_solve on this context,
+ * measured with CUDA events around its phases on the context's stream:
+ *   init_ms   initialisation (r_0 ... first reduction)
+ *   loop_ms   the iteration loop (all K iterations, including the device-
+ *             side loop control)
+ *   iters     K
+ * Any pointer may be NULL.
+ */
+int prcg_last_timing(const prcg_ctx* ctx, float* init_ms, float* loop_ms, int* iters);
+
+/*
+ * prcg_last_launches -- number of this library's kernels the last
+ * prcg_solve launched (initialisation sweeps, iteration sweeps including the
+ * no-op sweeps after convergence within the last loop body, loop-control
+ * kernels, and the optional true-residual sweep).
+ */
+int prcg_last_launches(const prcg_ctx* ctx, int64_t* kernels);
+
+/* prcg_destroy -- free the context and everything it owns; NULL is a no-op. */
+int prcg_destroy(prcg_ctx* ctx);
+
+/*
+ * prcg_last_error -- message describing the last failure on ctx (or of the
+ * last failed create when ctx is NULL).  Valid until the next call on ctx.
+ */
+const char* prcg_last_error(const prcg_ctx* ctx);
+
+/* prcg_n -- the number of unknowns of the context (or -1 for NULL). */
+int64_t prcg_n(const prcg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PRCG_H */

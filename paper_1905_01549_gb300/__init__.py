@@ -1,0 +1,105 @@
+"""GB300-native predict-and-recompute conjugate gradients (Chen & Carson).
+
+The solver is the CUDA library libprcg.so (C ABI in include/prcg.h); this
+package loads it with ctypes (``binding``) and wraps a context in a small
+``Solver`` class that takes torch tensors.  PyTorch is used only to hold
+device memory and name streams.  Importing the package fails if the library
+has not been built (``paper_1905_01549_gb300.build.build()``).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import binding
+from .binding import (PRCG_BREAKDOWN, PRCG_NOT_CONVERGED, PRCG_OK, PrcgError,  # noqa: F401
+                      VARIANT_IDS)
+
+binding.load()
+
+PRECONDS = {"none": binding.PRCG_PRECOND_NONE, "jacobi": binding.PRCG_PRECOND_JACOBI}
+
+
+@dataclasses.dataclass
+class SolveResult:
+    x: object                 # x_K (same kind of array as the x passed / a new CUDA tensor)
+    iters: int                # K
+    status: int               # PRCG_OK / PRCG_NOT_CONVERGED / PRCG_BREAKDOWN
+    hist: Optional[np.ndarray]  # ||r_k|| / ||b||, k = 0..K
+    true_relres: Optional[float]
+    init_ms: float
+    loop_ms: float
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Solver:
+    """One library context (operator + preconditioner) for repeated solves."""
+
+    def __init__(self, handle: int, n: int):
+        self.handle = handle
+        self.n = n
+
+    @classmethod
+    def from_csr(cls, row_ptr, col_idx, vals, precond: str = "none", stream=None) -> "Solver":
+        n = len(row_ptr) - 1
+        nnz = len(vals)
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32) if isinstance(row_ptr, np.ndarray) else row_ptr
+        col_idx = np.ascontiguousarray(col_idx, dtype=np.int32) if isinstance(col_idx, np.ndarray) else col_idx
+        vals = np.ascontiguousarray(vals, dtype=np.float64) if isinstance(vals, np.ndarray) else vals
+        h = binding.prcg_create_csr(n, nnz, row_ptr, col_idx, vals, PRECONDS[precond], stream)
+        return cls(h, n)
+
+    @classmethod
+    def from_stencil(cls, dims: Sequence[int], face_coeff=None, diag_shift: float = 0.0,
+                     precond: str = "none", stream=None) -> "Solver":
+        dims = tuple(int(d) for d in dims)
+        nx, ny = dims[0], dims[1]
+        nz = dims[2] if len(dims) == 3 else 1
+        if isinstance(face_coeff, np.ndarray):
+            face_coeff = np.ascontiguousarray(face_coeff, dtype=np.float64)
+        h = binding.prcg_create_stencil(len(dims), nx, ny, nz, face_coeff, diag_shift,
+                                        PRECONDS[precond], stream)
+        return cls(h, nx * ny * nz)
+
+    def solve(self, b, x0=None, variant: str = "pr", tol: float = 1e-10,
+              maxit: Optional[int] = None, history: bool = False,
+              true_relres: bool = False) -> SolveResult:
+        """Solve A x = b.  b / x0 may be CUDA tensors, CPU tensors or numpy arrays.
+
+        Without x0 a zero CUDA tensor is used and returned as x; with x0 the
+        result overwrites x0 in place."""
+        torch = _torch()
+        if maxit is None:
+            maxit = 2 * self.n
+        if isinstance(b, np.ndarray):
+            b = np.ascontiguousarray(b, dtype=np.float64)
+        x = x0 if x0 is not None else torch.zeros(self.n, dtype=torch.float64, device="cuda")
+        hist = np.empty(maxit + 1) if history else None
+        status, iters, trr = binding.prcg_solve(self.handle, VARIANT_IDS[variant], b, x, tol, maxit,
+                                                hist, true_relres)
+        init_ms, loop_ms, _ = binding.prcg_last_timing(self.handle)
+        return SolveResult(x, iters, status, None if hist is None else hist[:iters + 1], trr,
+                           init_ms, loop_ms)
+
+    def close(self):
+        if self.handle:
+            binding.prcg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,169 @@
+"""ctypes binding of libprcg.so: the C ABI of include/prcg.h, same names.
+
+Argument marshalling only: arrays are passed as raw pointers (torch tensors
+on the GPU or the host, or numpy arrays), every computation happens in the
+CUDA library.  There is no CPU fallback: if the library is missing the
+import of this module fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libprcg.so")
+
+PRCG_HS, PRCG_PR, PRCG_PIPE_PR, PRCG_M, PRCG_PIPE_M, PRCG_CGCG, PRCG_GV = range(7)
+PRCG_PRECOND_NONE, PRCG_PRECOND_JACOBI = 0, 1
+PRCG_OK, PRCG_NOT_CONVERGED, PRCG_BREAKDOWN = 0, 1, 2
+PRCG_ERR_INVALID, PRCG_ERR_CUDA, PRCG_ERR_OOM, PRCG_ERR_TIMEOUT, PRCG_ERR_UNSUPPORTED = \
+    -1, -2, -3, -4, -5
+
+VARIANT_IDS = {"hs": PRCG_HS, "pr": PRCG_PR, "pipe_pr": PRCG_PIPE_PR, "m": PRCG_M,
+               "pipe_m": PRCG_PIPE_M, "cgcg": PRCG_CGCG, "gv": PRCG_GV}
+STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_INVALID", -2: "ERR_CUDA",
+                -3: "ERR_OOM", -4: "ERR_TIMEOUT", -5: "ERR_UNSUPPORTED"}
+
+# every symbol include/prcg.h declares
+EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_solve", "prcg_last_timing",
+           "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n")
+
+
+class PrcgError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_c_int_p = ctypes.POINTER(ctypes.c_int)
+_c_double_p = ctypes.POINTER(ctypes.c_double)
+_c_float_p = ctypes.POINTER(ctypes.c_float)
+
+_lib: Optional[ctypes.CDLL] = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libprcg.so and declare the signatures; raises if it is not built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1905_01549_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    lib.prcg_create_csr.argtypes = [ctypes.POINTER(vp), ctypes.c_int64, ctypes.c_int64, vp, vp, vp,
+                                    ctypes.c_int, vp]
+    lib.prcg_create_csr.restype = ctypes.c_int
+    lib.prcg_create_stencil.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int64,
+                                        ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_double,
+                                        ctypes.c_int, vp]
+    lib.prcg_create_stencil.restype = ctypes.c_int
+    lib.prcg_solve.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_int, vp,
+                               _c_int_p, _c_double_p]
+    lib.prcg_solve.restype = ctypes.c_int
+    lib.prcg_last_timing.argtypes = [vp, _c_float_p, _c_float_p, _c_int_p]
+    lib.prcg_last_timing.restype = ctypes.c_int
+    lib.prcg_last_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.prcg_last_launches.restype = ctypes.c_int
+    lib.prcg_destroy.argtypes = [vp]
+    lib.prcg_destroy.restype = ctypes.c_int
+    lib.prcg_last_error.argtypes = [vp]
+    lib.prcg_last_error.restype = ctypes.c_char_p
+    lib.prcg_n.argtypes = [vp]
+    lib.prcg_n.restype = ctypes.c_int64
+    _lib = lib
+    return lib
+
+
+def ptr(a) -> Optional[int]:
+    """Raw address of a torch tensor / numpy array (None passes NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("array must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _check(code: int, ctx=None):
+    if code < 0:
+        msg = load().prcg_last_error(ctx).decode(errors="replace")
+        raise PrcgError(code, msg)
+    return code
+
+
+def prcg_create_csr(n, nnz, row_ptr, col_idx, vals, precond=PRCG_PRECOND_NONE, stream=None):
+    """Create a CSR context; returns the opaque handle (an int)."""
+    lib = load()
+    out = ctypes.c_void_p()
+    rc = lib.prcg_create_csr(ctypes.byref(out), int(n), int(nnz), ptr(row_ptr), ptr(col_idx),
+                             ptr(vals), int(precond), _stream_ptr(stream))
+    _check(rc, None)
+    return out.value
+
+
+def prcg_create_stencil(dim, nx, ny, nz, face_coeff=None, diag_shift=0.0,
+                        precond=PRCG_PRECOND_NONE, stream=None):
+    """Create a matrix-free stencil context; returns the opaque handle."""
+    lib = load()
+    out = ctypes.c_void_p()
+    rc = lib.prcg_create_stencil(ctypes.byref(out), int(dim), int(nx), int(ny), int(nz),
+                                 ptr(face_coeff), float(diag_shift), int(precond),
+                                 _stream_ptr(stream))
+    _check(rc, None)
+    return out.value
+
+
+def prcg_solve(ctx, variant, b, x, tol, maxit, residual_history=None, want_true_relres=False):
+    """Solve in place (x: in x_0, out x_K); returns (status, iters, true_relres or None)."""
+    lib = load()
+    iters = ctypes.c_int(0)
+    trr = ctypes.c_double(float("nan"))
+    rc = lib.prcg_solve(ctx, int(variant), ptr(b), ptr(x), float(tol), int(maxit),
+                        ptr(residual_history), ctypes.byref(iters),
+                        ctypes.byref(trr) if want_true_relres else None)
+    _check(rc, ctx)
+    return rc, iters.value, (trr.value if want_true_relres else None)
+
+
+def prcg_last_timing(ctx):
+    """(init_ms, loop_ms, iters) of the last solve, from CUDA events."""
+    lib = load()
+    a, b, k = ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
+    _check(lib.prcg_last_timing(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)), ctx)
+    return a.value, b.value, k.value
+
+
+def prcg_last_launches(ctx) -> int:
+    """Kernels the last solve launched."""
+    k = ctypes.c_int64()
+    _check(load().prcg_last_launches(ctx, ctypes.byref(k)), ctx)
+    return k.value
+
+
+def prcg_destroy(ctx):
+    return load().prcg_destroy(ctx)
+
+
+def prcg_last_error(ctx=None) -> str:
+    return load().prcg_last_error(ctx).decode(errors="replace")
+
+
+def prcg_n(ctx) -> int:
+    return int(load().prcg_n(ctx))

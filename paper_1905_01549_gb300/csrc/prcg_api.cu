@@ -1,0 +1,632 @@
+// C ABI of the predict-and-recompute CG library (declared in include/prcg.h).
+//
+// A context owns device copies of the operator, the Jacobi diagonal, the
+// iteration vectors (double-buffered where a sweep gathers them), the
+// device-resident scalar block and, per variant, one instantiated CUDA
+// graph: the initialisation sweeps followed by a device-side while loop
+// whose body runs a fixed number of fused iteration sweeps and a one-thread
+// kernel that decides whether to go on.  A solve is therefore one graph
+// launch with no host round trip per iteration.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "../../include/prcg.h"
+#include "prcg_launch.cuh"
+
+namespace prcg {
+LaunchFn launcher_csr(int op_kind, int pc_kind);
+LaunchFn launcher_st(int op_kind, int pc_kind);
+LaunchFn launcher_vc(int op_kind, int pc_kind);
+
+LaunchFn launcher_for(int op_kind, int pc_kind) {
+  if (op_kind == OP_CSR) return launcher_csr(op_kind, pc_kind);
+  if (op_kind == OP_ST2 || op_kind == OP_ST3) return launcher_st(op_kind, pc_kind);
+  return launcher_vc(op_kind, pc_kind);
+}
+
+// ---------------------------------------------------------------- set-up kernels
+__global__ void k_check_csr(const int* rp, const int* ci, int n, int nnz, int* bad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int e0 = rp[i], e1 = rp[i + 1];
+    if (e0 < 0 || e1 < e0 || e1 > nnz) {
+      atomicOr(bad, 1);
+      continue;
+    }
+    for (int e = e0; e < e1; ++e) {
+      const int j = ci[e];
+      if (j < 0 || j >= n) atomicOr(bad, 2);
+    }
+  }
+}
+
+// d_i = 1 / a_ii (Section 4: Jacobi); flags a missing or non-positive a_ii.
+__global__ void k_csr_jacobi(const int* rp, const int* ci, const double* va, int n, double* d,
+                             int* bad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double a = 0.0;
+    for (int e = rp[i]; e < rp[i + 1]; ++e)
+      if (ci[e] == i) a += va[e];
+    if (!(a > 0.0) || !isfinite(a)) {
+      atomicOr(bad, 4);
+      d[i] = 0.0;
+    } else {
+      d[i] = 1.0 / a;
+    }
+  }
+}
+
+// Diagonal of the variable-coefficient operator: the sum of the cell's face
+// coefficients (x-, x+, y-, y+, z-, z+) plus the shift; optionally 1 / a_ii.
+__global__ void k_vc_diag(int dim, int nx, int ny, int nz, const double* fx, const double* fy,
+                          const double* fz, double shift, double* adiag, double* d, int* bad) {
+  const int n = nx * ny * nz;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int x = i % nx, yz = i / nx, y = yz % ny, z = yz / ny;
+    double a = fx[yz * (nx + 1) + x] + fx[yz * (nx + 1) + x + 1];
+    a = a + fy[(z * (ny + 1) + y) * nx + x];
+    a = a + fy[(z * (ny + 1) + y + 1) * nx + x];
+    if (dim == 3) {
+      a = a + fz[i];
+      a = a + fz[i + nx * ny];
+    }
+    a = a + shift;
+    adiag[i] = a;
+    if (d) {
+      if (!(a > 0.0) || !isfinite(a)) {
+        atomicOr(bad, 4);
+        d[i] = 0.0;
+      } else {
+        d[i] = 1.0 / a;
+      }
+    }
+  }
+}
+
+// Body-end control of the device-side while loop.
+__global__ void k_loop_control(cudaGraphConditionalHandle h, DevState* S) {
+  const unsigned b = S->bodies + 1u;
+  S->bodies = b;
+  bool more = S->done == 0;
+  if (more && (int)b >= S->maxbodies) {
+    S->status = PRCG_ERR_TIMEOUT;
+    S->done = 1;
+    more = false;
+  }
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+}  // namespace prcg
+
+using namespace prcg;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct VariantGraph {
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  int chunk = 0;
+};
+
+}  // namespace
+
+struct prcg_ctx {
+  int device = 0;
+  cudaStream_t user = nullptr;
+  cudaStream_t cs = nullptr;     // internal stream all work runs on
+  cudaStream_t bs = nullptr;     // capture stream for loop bodies
+  cudaEvent_t ev_user = nullptr, ev_start = nullptr, ev_init = nullptr, ev_loop = nullptr;
+  Plan plan{};
+  LaunchFn launch = nullptr;
+  int n = 0;
+  int precond = 0;
+  double* pool = nullptr;        // all n-length vectors
+  int* ipool = nullptr;          // CSR indices
+  double* vpool = nullptr;       // CSR values / faces / diagonals
+  double* partials = nullptr;
+  DevState* S = nullptr;
+  DevState* hS = nullptr;        // pinned mirror
+  double* hist = nullptr;
+  int hist_cap = 0;
+  int* dbad = nullptr;
+  VariantGraph graphs[8];
+  bool use_graph = true;
+  float t_init = 0.f, t_loop = 0.f;
+  int last_iters = 0;
+  int64_t last_launches = 0;
+  int64_t host_loop_launches = 0;
+  std::string err;
+};
+
+namespace {
+
+int set_err(prcg_ctx* c, int code, const std::string& msg) {
+  if (c)
+    c->err = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+int cuda_err(prcg_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return set_err(c, e == cudaErrorMemoryAllocation ? PRCG_ERR_OOM : PRCG_ERR_CUDA, m);
+}
+
+#define CK(call)                                    \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_err(c, e_, #call); \
+  } while (0)
+
+int ctx_init_common(prcg_ctx* c, void* stream, int n) {
+  c->n = n;
+  c->user = (cudaStream_t)stream;
+  CK(cudaGetDevice(&c->device));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+  c->plan.sms = sms;
+  CK(cudaStreamCreateWithFlags(&c->cs, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&c->bs, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming));
+  CK(cudaEventCreate(&c->ev_start));
+  CK(cudaEventCreate(&c->ev_init));
+  CK(cudaEventCreate(&c->ev_loop));
+  // 17 n-vectors: x, b, t, d and two buffers each of r, r~, p, s, s~, w, u
+  const size_t nv = 17;
+  CK(cudaMalloc(&c->pool, nv * (size_t)n * sizeof(double)));
+  double* q = c->pool;
+  auto take = [&]() {
+    double* r = q;
+    q += n;
+    return r;
+  };
+  Vecs& V = c->plan.v;
+  V.x = take();
+  V.b = take();
+  V.t = take();
+  double* d = take();
+  for (int k = 0; k < 2; ++k) {
+    V.r[k] = take();
+    V.rt[k] = take();
+    V.p[k] = take();
+    V.s[k] = take();
+    V.st[k] = take();
+    V.w[k] = take();
+    V.u[k] = take();
+  }
+  c->plan.pc.d = d;
+  CK(cudaMalloc(&c->partials, (size_t)kMaxGrid * kMaxNV * sizeof(double)));
+  CK(cudaMalloc(&c->S, sizeof(DevState)));
+  CK(cudaMemset(c->S, 0, sizeof(DevState)));
+  CK(cudaMallocHost(&c->hS, sizeof(DevState)));
+  CK(cudaMalloc(&c->dbad, sizeof(int)));
+  CK(cudaMemset(c->dbad, 0, sizeof(int)));
+  c->plan.S = c->S;
+  c->plan.partials = c->partials;
+  const char* ng = getenv("PRCG_NO_GRAPH");
+  c->use_graph = !(ng && ng[0] == '1');
+  return PRCG_OK;
+}
+
+// Order the internal stream after everything already queued on the user's.
+int wait_user(prcg_ctx* c) {
+  CK(cudaEventRecord(c->ev_user, c->user));
+  CK(cudaStreamWaitEvent(c->cs, c->ev_user, 0));
+  return PRCG_OK;
+}
+
+int check_bad(prcg_ctx* c, const char* what) {
+  int bad = 0;
+  CK(cudaMemcpyAsync(&bad, c->dbad, sizeof(int), cudaMemcpyDeviceToHost, c->cs));
+  CK(cudaStreamSynchronize(c->cs));
+  if (bad) {
+    char m[160];
+    snprintf(m, sizeof m, "%s (flags %d: 1 row_ptr, 2 col_idx, 4 diagonal)", what, bad);
+    return set_err(c, PRCG_ERR_INVALID, m);
+  }
+  return PRCG_OK;
+}
+
+void destroy_graphs(prcg_ctx* c) {
+  for (auto& g : c->graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    if (g.graph) cudaGraphDestroy(g.graph);
+    g.exec = nullptr;
+    g.graph = nullptr;
+  }
+}
+
+int launch_init(prcg_ctx* c, int variant, cudaStream_t st) {
+  const bool pipe = variant == V_PIPE || variant == V_PIPE_M || variant == V_GV;
+  CK(c->launch(c->plan, PH_INIT_A, variant, 0, 0, st));
+  CK(c->launch(c->plan, PH_INIT_B, variant, 0, 0, st));
+  if (pipe) CK(c->launch(c->plan, PH_INIT_C, variant, 0, 0, st));
+  return PRCG_OK;
+}
+
+// One iteration of `variant` reading buffer qr and writing buffer qw.
+int launch_iter(prcg_ctx* c, int variant, int qr, int qw, cudaStream_t st) {
+  switch (variant) {
+    case V_HS:
+      CK(c->launch(c->plan, PH_HS_A, variant, qr, qw, st));
+      CK(c->launch(c->plan, PH_HS_B, variant, qr, qw, st));
+      break;
+    case V_PR:
+    case V_M:
+      CK(c->launch(c->plan, PH_PR, variant, qr, qw, st));
+      break;
+    case V_PIPE:
+    case V_PIPE_M:
+      CK(c->launch(c->plan, PH_PIPE, variant, qr, qw, st));
+      break;
+    default:
+      return set_err(c, PRCG_ERR_UNSUPPORTED, "variant not built on the GPU path");
+  }
+  return PRCG_OK;
+}
+
+int chunk_for(prcg_ctx* c) { return c->n >= (1 << 20) ? 2 : 16; }
+
+int build_graph(prcg_ctx* c, int variant) {
+  VariantGraph& G = c->graphs[variant];
+  if (G.exec) return PRCG_OK;
+  const int chunk = chunk_for(c);
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  G.graph = g;
+  CK(cudaStreamBeginCaptureToGraph(c->cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  int rc = launch_init(c, variant, c->cs);
+  if (rc == PRCG_OK) {
+    cudaError_t e = cudaEventRecordWithFlags(c->ev_init, c->cs, cudaEventRecordExternal);
+    if (e != cudaSuccess) rc = cuda_err(c, e, "event record in capture");
+  }
+  cudaGraphConditionalHandle h;
+  cudaGraphNode_t cond = nullptr;
+  if (rc == PRCG_OK) {
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaGraph_t cg = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(c->cs, &cst, nullptr, &cg, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams cp = {cudaGraphNodeTypeConditional};
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    if (e == cudaSuccess) e = cudaGraphAddNode(&cond, g, deps, nullptr, ndeps, &cp);
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(c->cs, &cond, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) {
+      rc = cuda_err(c, e, "conditional node");
+    } else {
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(c->bs, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) rc = cuda_err(c, e, "body capture");
+      for (int m = 0; rc == PRCG_OK && m < chunk; ++m) rc = launch_iter(c, variant, m & 1, (m + 1) & 1, c->bs);
+      if (rc == PRCG_OK) {
+        k_loop_control<<<1, 1, 0, c->bs>>>(h, c->S);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_err(c, e, "loop control launch");
+      }
+      cudaGraph_t bo = nullptr;
+      cudaError_t e2 = cudaStreamEndCapture(c->bs, &bo);
+      if (rc == PRCG_OK && e2 != cudaSuccess) rc = cuda_err(c, e2, "end body capture");
+    }
+  }
+  if (rc == PRCG_OK) {
+    cudaError_t e = cudaEventRecordWithFlags(c->ev_loop, c->cs, cudaEventRecordExternal);
+    if (e != cudaSuccess) rc = cuda_err(c, e, "event record in capture");
+  }
+  cudaGraph_t go = nullptr;
+  cudaError_t e3 = cudaStreamEndCapture(c->cs, &go);
+  if (rc == PRCG_OK && e3 != cudaSuccess) rc = cuda_err(c, e3, "end capture");
+  if (rc == PRCG_OK) {
+    cudaError_t e = cudaGraphInstantiate(&G.exec, g, 0);
+    if (e != cudaSuccess) rc = cuda_err(c, e, "graph instantiate");
+  }
+  if (rc != PRCG_OK) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    cudaGraphDestroy(g);
+    G.exec = nullptr;
+    G.graph = nullptr;
+    cudaGetLastError();
+    return rc;
+  }
+  G.chunk = chunk;
+  return PRCG_OK;
+}
+
+// Host-driven loop, used when graphs are disabled (PRCG_NO_GRAPH=1) or fail
+// to build: the same sweeps launched directly, with the status read back
+// after every chunk.
+int run_host_loop(prcg_ctx* c, int variant, int maxit) {
+  const int chunk = chunk_for(c);
+  int rc = launch_init(c, variant, c->cs);
+  if (rc != PRCG_OK) return rc;
+  CK(cudaEventRecord(c->ev_init, c->cs));
+  for (int it = 0; it <= maxit; it += chunk) {
+    CK(cudaMemcpyAsync(c->hS, c->S, sizeof(DevState), cudaMemcpyDeviceToHost, c->cs));
+    CK(cudaStreamSynchronize(c->cs));
+    if (c->hS->done) break;
+    for (int m = 0; m < chunk; ++m) {
+      rc = launch_iter(c, variant, m & 1, (m + 1) & 1, c->cs);
+      if (rc != PRCG_OK) return rc;
+      c->host_loop_launches += variant == V_HS ? 2 : 1;
+    }
+  }
+  CK(cudaEventRecord(c->ev_loop, c->cs));
+  return PRCG_OK;
+}
+
+int copy_in(prcg_ctx* c, void* dst, const void* src, size_t bytes) {
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->cs));
+  return PRCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int prcg_create_csr(prcg_ctx** out, int64_t n, int64_t nnz, const int32_t* row_ptr,
+                    const int32_t* col_idx, const double* vals, int precond, void* cuda_stream) {
+  prcg_ctx* c = nullptr;
+  if (!out) return set_err(nullptr, PRCG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n >= (int64_t)1 << 31 || nnz < 0 || nnz >= (int64_t)1 << 31)
+    return set_err(nullptr, PRCG_ERR_INVALID, "n or nnz out of range");
+  if (!row_ptr || (nnz > 0 && (!col_idx || !vals)))
+    return set_err(nullptr, PRCG_ERR_INVALID, "NULL array");
+  if (precond != PRCG_PRECOND_NONE && precond != PRCG_PRECOND_JACOBI)
+    return set_err(nullptr, PRCG_ERR_INVALID, "unknown preconditioner");
+  c = new prcg_ctx();
+  int rc = ctx_init_common(c, cuda_stream, (int)n);
+  if (rc != PRCG_OK) {
+    g_create_error = c->err;
+    prcg_destroy(c);
+    return rc;
+  }
+  auto fail = [&](int code) {
+    g_create_error = c->err;
+    prcg_destroy(c);
+    return code;
+  };
+  const size_t idx_elems = (size_t)(n + 1) + (size_t)nnz + 4;  // +4: room for vector loads
+  if (cudaMalloc(&c->ipool, idx_elems * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&c->vpool, ((size_t)nnz + 2) * sizeof(double)) != cudaSuccess)
+    return fail(set_err(c, PRCG_ERR_OOM, "CSR allocation failed"));
+  int* rp = c->ipool;
+  int* ci = c->ipool + (n + 1);
+  double* va = c->vpool;
+  if ((rc = wait_user(c)) != PRCG_OK) return fail(rc);
+  if ((rc = copy_in(c, rp, row_ptr, (size_t)(n + 1) * sizeof(int))) != PRCG_OK) return fail(rc);
+  if (nnz > 0) {
+    if ((rc = copy_in(c, ci, col_idx, (size_t)nnz * sizeof(int))) != PRCG_OK) return fail(rc);
+    if ((rc = copy_in(c, va, vals, (size_t)nnz * sizeof(double))) != PRCG_OK) return fail(rc);
+  }
+  int ends[2] = {0, 0};
+  cudaMemcpyAsync(&ends[0], rp, sizeof(int), cudaMemcpyDeviceToHost, c->cs);
+  cudaMemcpyAsync(&ends[1], rp + n, sizeof(int), cudaMemcpyDeviceToHost, c->cs);
+  if (cudaStreamSynchronize(c->cs) != cudaSuccess) return fail(cuda_err(c, cudaGetLastError(), "copy"));
+  if (ends[0] != 0 || ends[1] != nnz) return fail(set_err(c, PRCG_ERR_INVALID, "row_ptr[0] != 0 or row_ptr[n] != nnz"));
+  k_check_csr<<<c->plan.sms * 4, 256, 0, c->cs>>>(rp, ci, (int)n, (int)nnz, c->dbad);
+  if ((rc = check_bad(c, "invalid CSR structure")) != PRCG_OK) return fail(rc);
+  c->plan.op.kind = OP_CSR;
+  c->plan.op.n = (int)n;
+  c->plan.op.rp = rp;
+  c->plan.op.ci = ci;
+  c->plan.op.va = va;
+  c->precond = precond;
+  c->plan.pc.kind = PC_NONE;
+  if (precond == PRCG_PRECOND_JACOBI) {
+    c->plan.pc.kind = PC_VEC;
+    k_csr_jacobi<<<c->plan.sms * 4, 256, 0, c->cs>>>(rp, ci, va, (int)n,
+                                                    const_cast<double*>(c->plan.pc.d), c->dbad);
+    if ((rc = check_bad(c, "Jacobi needs a positive diagonal")) != PRCG_OK) return fail(rc);
+  }
+  c->launch = launcher_for(c->plan.op.kind, c->plan.pc.kind);
+  if (!c->launch) return fail(set_err(c, PRCG_ERR_UNSUPPORTED, "operator not built"));
+  *out = c;
+  return PRCG_OK;
+}
+
+int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t nz,
+                        const double* face_coeff, double diag_shift, int precond,
+                        void* cuda_stream) {
+  if (!out) return set_err(nullptr, PRCG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (dim != 2 && dim != 3) return set_err(nullptr, PRCG_ERR_INVALID, "dim must be 2 or 3");
+  if (dim == 2) nz = 1;
+  if (nx < 1 || ny < 1 || nz < 1) return set_err(nullptr, PRCG_ERR_INVALID, "grid size < 1");
+  const int64_t n = nx * ny * nz;
+  if (n + nx * ny >= (int64_t)1 << 31 || nx >= (1 << 30) || ny >= (1 << 30))
+    return set_err(nullptr, PRCG_ERR_INVALID, "grid too large");
+  if (precond != PRCG_PRECOND_NONE && precond != PRCG_PRECOND_JACOBI)
+    return set_err(nullptr, PRCG_ERR_INVALID, "unknown preconditioner");
+  if (!(diag_shift >= 0.0) || !std::isfinite(diag_shift))
+    return set_err(nullptr, PRCG_ERR_INVALID, "diag_shift must be finite and >= 0");
+  prcg_ctx* c = new prcg_ctx();
+  int rc = ctx_init_common(c, cuda_stream, (int)n);
+  auto fail = [&](int code) {
+    g_create_error = c->err;
+    prcg_destroy(c);
+    return code;
+  };
+  if (rc != PRCG_OK) return fail(rc);
+  OpDesc& op = c->plan.op;
+  op.n = (int)n;
+  op.nx = (int)nx;
+  op.ny = (int)ny;
+  op.nz = (int)nz;
+  c->precond = precond;
+  if (!face_coeff) {
+    op.kind = dim == 2 ? OP_ST2 : OP_ST3;
+    op.cdiag = 2.0 * dim + diag_shift;
+    c->plan.pc.kind = PC_NONE;
+    if (precond == PRCG_PRECOND_JACOBI) {
+      c->plan.pc.kind = PC_SCALAR;
+      c->plan.pc.dscalar = 1.0 / op.cdiag;
+    }
+  } else {
+    op.kind = dim == 2 ? OP_VC2 : OP_VC3;
+    const size_t nfx = (size_t)nz * ny * (nx + 1), nfy = (size_t)nz * (ny + 1) * nx;
+    const size_t nfz = dim == 3 ? (size_t)(nz + 1) * ny * nx : 0;
+    const size_t nf = nfx + nfy + nfz;
+    if (cudaMalloc(&c->vpool, (nf + (size_t)n + 2) * sizeof(double)) != cudaSuccess)
+      return fail(set_err(c, PRCG_ERR_OOM, "face allocation failed"));
+    if ((rc = wait_user(c)) != PRCG_OK) return fail(rc);
+    if ((rc = copy_in(c, c->vpool, face_coeff, nf * sizeof(double))) != PRCG_OK) return fail(rc);
+    op.fx = c->vpool;
+    op.fy = c->vpool + nfx;
+    op.fz = dim == 3 ? c->vpool + nfx + nfy : nullptr;
+    double* adiag = c->vpool + nf;
+    op.adiag = adiag;
+    double* d = precond == PRCG_PRECOND_JACOBI ? const_cast<double*>(c->plan.pc.d) : nullptr;
+    k_vc_diag<<<c->plan.sms * 4, 256, 0, c->cs>>>(dim, (int)nx, (int)ny, (int)nz, op.fx, op.fy,
+                                                 op.fz, diag_shift, adiag, d, c->dbad);
+    if ((rc = check_bad(c, "Jacobi needs a positive diagonal")) != PRCG_OK) return fail(rc);
+    c->plan.pc.kind = precond == PRCG_PRECOND_JACOBI ? PC_VEC : PC_NONE;
+  }
+  c->launch = launcher_for(op.kind, c->plan.pc.kind);
+  if (!c->launch) return fail(set_err(c, PRCG_ERR_UNSUPPORTED, "operator not built"));
+  *out = c;
+  return PRCG_OK;
+}
+
+int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol, int maxit,
+               double* residual_history, int* iters_out, double* final_true_relres_out) {
+  if (!c) return set_err(nullptr, PRCG_ERR_INVALID, "ctx is NULL");
+  if (!b || !x) return set_err(c, PRCG_ERR_INVALID, "b or x is NULL");
+  if (!(tol >= 0.0) || maxit < 0) return set_err(c, PRCG_ERR_INVALID, "tol < 0 or maxit < 0");
+  if (variant < 0 || variant > 6) return set_err(c, PRCG_ERR_INVALID, "unknown variant");
+  if (variant == V_CGCG || variant == V_GV)
+    return set_err(c, PRCG_ERR_UNSUPPORTED, "CG-CG and GV-CG are not built on the GPU path");
+  const int n = c->n;
+  int rc;
+  if (c->hist_cap < maxit + 1) {
+    if (c->hist) cudaFree(c->hist);
+    c->hist = nullptr;
+    c->hist_cap = 0;
+    CK(cudaMalloc(&c->hist, (size_t)(maxit + 1) * sizeof(double)));
+    c->hist_cap = maxit + 1;
+  }
+  bool graph = c->use_graph;
+  if (graph && build_graph(c, variant) != PRCG_OK) graph = false;  // fall back to the host loop
+  const int chunk = graph ? c->graphs[variant].chunk : chunk_for(c);
+  if ((rc = wait_user(c)) != PRCG_OK) return rc;
+  if ((rc = copy_in(c, (void*)c->plan.v.b, b, (size_t)n * sizeof(double))) != PRCG_OK) return rc;
+  if ((rc = copy_in(c, c->plan.v.x, x, (size_t)n * sizeof(double))) != PRCG_OK) return rc;
+  DevState& h = *c->hS;
+  memset(&h, 0, sizeof h);
+  h.tol = tol;
+  h.hist = c->hist;
+  h.maxit = maxit;
+  h.maxbodies = maxit / chunk + 3;
+  h.status = kRunning;
+  CK(cudaMemcpyAsync(c->S, &h, sizeof h, cudaMemcpyHostToDevice, c->cs));
+  CK(cudaEventRecord(c->ev_start, c->cs));
+  if (graph) {
+    CK(cudaGraphLaunch(c->graphs[variant].exec, c->cs));
+  } else {
+    c->host_loop_launches = 0;
+    if ((rc = run_host_loop(c, variant, maxit)) != PRCG_OK) return rc;
+  }
+  CK(cudaMemcpyAsync(&h, c->S, sizeof h, cudaMemcpyDeviceToHost, c->cs));
+  CK(cudaStreamSynchronize(c->cs));
+  const int K = h.k;
+  {
+    const bool pipe = variant == V_PIPE || variant == V_PIPE_M;
+    const int64_t per_iter = variant == V_HS ? 2 : 1;
+    int64_t launches = pipe ? 3 : 2;
+    if (graph)
+      launches += (int64_t)h.bodies * (chunk * per_iter + 1);
+    else
+      launches += c->host_loop_launches;
+    if (final_true_relres_out) launches += 1;
+    c->last_launches = launches;
+  }
+  const int status = h.status;
+  if (status == kRunning) return set_err(c, PRCG_ERR_CUDA, "device loop ended without a status");
+  if (status < 0) return set_err(c, status, "device loop exceeded its iteration limit");
+  if (h.zero_rhs) CK(cudaMemsetAsync(c->plan.v.x, 0, (size_t)n * sizeof(double), c->cs));
+  CK(cudaMemcpyAsync(x, c->plan.v.x, (size_t)n * sizeof(double), cudaMemcpyDefault, c->cs));
+  if (residual_history)
+    CK(cudaMemcpyAsync(residual_history, c->hist, (size_t)(K + 1) * sizeof(double),
+                       cudaMemcpyDefault, c->cs));
+  if (final_true_relres_out) {
+    if (h.zero_rhs) {
+      *final_true_relres_out = 0.0;
+    } else {
+      if ((rc = (c->launch(c->plan, PH_TRUE_RES, variant, 0, 0, c->cs) == cudaSuccess
+                     ? PRCG_OK
+                     : cuda_err(c, cudaGetLastError(), "true residual"))) != PRCG_OK)
+        return rc;
+      DevState h2;
+      CK(cudaMemcpyAsync(&h2, c->S, sizeof h2, cudaMemcpyDeviceToHost, c->cs));
+      CK(cudaStreamSynchronize(c->cs));
+      *final_true_relres_out = sqrt(h2.eta) / sqrt(h2.nu_pred);
+    }
+  }
+  CK(cudaStreamSynchronize(c->cs));
+  float ti = 0.f, tl = 0.f;
+  if (cudaEventElapsedTime(&ti, c->ev_start, c->ev_init) != cudaSuccess) ti = -1.f;
+  if (cudaEventElapsedTime(&tl, c->ev_init, c->ev_loop) != cudaSuccess) tl = -1.f;
+  cudaGetLastError();
+  c->t_init = ti;
+  c->t_loop = tl;
+  c->last_iters = K;
+  if (iters_out) *iters_out = K;
+  return status;
+}
+
+int prcg_last_timing(const prcg_ctx* c, float* init_ms, float* loop_ms, int* iters) {
+  if (!c) return PRCG_ERR_INVALID;
+  if (init_ms) *init_ms = c->t_init;
+  if (loop_ms) *loop_ms = c->t_loop;
+  if (iters) *iters = c->last_iters;
+  return PRCG_OK;
+}
+
+int prcg_last_launches(const prcg_ctx* c, int64_t* kernels) {
+  if (!c || !kernels) return PRCG_ERR_INVALID;
+  *kernels = c->last_launches;
+  return PRCG_OK;
+}
+
+int prcg_destroy(prcg_ctx* c) {
+  if (!c) return PRCG_OK;
+  if (c->cs) cudaStreamSynchronize(c->cs);
+  destroy_graphs(c);
+  if (c->pool) cudaFree(c->pool);
+  if (c->ipool) cudaFree(c->ipool);
+  if (c->vpool) cudaFree(c->vpool);
+  if (c->partials) cudaFree(c->partials);
+  if (c->S) cudaFree(c->S);
+  if (c->hS) cudaFreeHost(c->hS);
+  if (c->hist) cudaFree(c->hist);
+  if (c->dbad) cudaFree(c->dbad);
+  if (c->ev_user) cudaEventDestroy(c->ev_user);
+  if (c->ev_start) cudaEventDestroy(c->ev_start);
+  if (c->ev_init) cudaEventDestroy(c->ev_init);
+  if (c->ev_loop) cudaEventDestroy(c->ev_loop);
+  if (c->bs) cudaStreamDestroy(c->bs);
+  if (c->cs) cudaStreamDestroy(c->cs);
+  delete c;
+  return PRCG_OK;
+}
+
+const char* prcg_last_error(const prcg_ctx* c) {
+  return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+int64_t prcg_n(const prcg_ctx* c) { return c ? (int64_t)c->n : -1; }
+
+}  // extern "C"

@@ -1,0 +1,168 @@
+// Shared device-side definitions of the predict-and-recompute CG library:
+// the device-resident scalar block, the plan of device pointers every
+// kernel receives, and the deterministic two-level grid reduction that
+// replaces the paper's global reduction (Table 1, C_gr).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace prcg {
+
+constexpr int kBlock = 256;             // threads per CTA for every sweep
+constexpr int kMaxGrid = 152 * 16;      // upper bound of CTAs of one sweep
+constexpr int kMaxNV = 8;               // doubles reduced per CTA
+constexpr int kRunning = -100;          // status while the loop runs
+
+enum Variant { V_HS = 0, V_PR = 1, V_PIPE = 2, V_M = 3, V_PIPE_M = 4, V_CGCG = 5, V_GV = 6 };
+
+// Device-resident scalar block (one per context).  Written by the last CTA
+// of each sweep after the grid reduction, read by every CTA of the next.
+struct DevState {
+  // values of the latest reduction
+  double nu, mu, sigma, gamma, rho, eta;
+  // scalars of the next vector sweep (Section 2.2.1: formed up front)
+  double alpha, beta, nu_pred;
+  double bnorm2;
+  // per-solve parameters
+  double tol;
+  double* hist;          // device array, >= maxit + 1 entries
+  int maxit;
+  int maxbodies;         // safety limit for the device-side while loop
+  // loop state
+  int k;                 // completed iterations
+  int status;            // kRunning until decided
+  int done;              // 1 once status is decided: every later sweep is a no-op
+  int zero_rhs;          // b == 0: the result is x = 0
+  unsigned arrive;       // CTAs that finished the current sweep
+  unsigned bodies;       // executions of the while-loop body
+};
+
+// Pointers of one context; kernels take what they need by value.
+struct Vecs {
+  double* x;
+  const double* b;
+  double* r[2];
+  double* rt[2];
+  double* p[2];
+  double* s[2];
+  double* st[2];
+  double* w[2];
+  double* u[2];
+  double* t;             // scratch vector (true residual, GV's t_k)
+};
+
+__device__ __forceinline__ double ldcs(const double* p) { return __ldcs(p); }
+__device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
+
+// Sum v[0..NV) over the CTA in a fixed order; the result is valid in thread 0.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int m = 0; m < NV; ++m) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[m] += __shfl_down_sync(0xffffffffu, v[m], off);
+  }
+  __syncthreads();  // sm may still be read by a previous call
+  if (lane == 0) {
+#pragma unroll
+    for (int m = 0; m < NV; ++m) sm[m * 32 + wid] = v[m];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+      double t = lane < nwarps ? sm[m * 32 + lane] : 0.0;
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+      v[m] = t;
+    }
+  }
+}
+
+// Grid-wide sum of v: each CTA writes its partial, the last CTA to arrive
+// adds all partials in CTA order (deterministic for a fixed grid) and
+// returns true with the totals in tot (thread 0).  No CTA ever waits.
+template <int NV>
+__device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, DevState* S,
+                                         double (&tot)[NV]) {
+  __shared__ double sm[NV * 32];
+  __shared__ int is_last;
+  block_sum<NV>(v, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int m = 0; m < NV; ++m) partials[blockIdx.x * NV + m] = v[m];
+    __threadfence();
+    unsigned t = atomicAdd(&S->arrive, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!is_last) return false;
+  __threadfence();
+  double acc[NV];
+#pragma unroll
+  for (int m = 0; m < NV; ++m) acc[m] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+#pragma unroll
+    for (int m = 0; m < NV; ++m) acc[m] += __ldcg(&partials[b * NV + m]);
+  }
+  block_sum<NV>(acc, sm);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int m = 0; m < NV; ++m) tot[m] = acc[m];
+    S->arrive = 0;
+  }
+  return true;
+}
+
+__device__ __forceinline__ bool finite(double v) { return isfinite(v); }
+
+// --------------------------------------------------------------------------
+// scalar steps, run by thread 0 of the last CTA of a sweep
+// --------------------------------------------------------------------------
+
+// Decide convergence for iteration k from rho_k = <r_k, r_k>; returns true
+// (and finishes the run) when ||r_k|| / ||b|| <= tol or k == maxit.
+__device__ __forceinline__ bool record_and_test(DevState* S, int k, double rho) {
+  S->k = k;
+  const double rel = sqrt(rho) / sqrt(S->bnorm2);
+  if (S->hist) S->hist[k] = rel;
+  if (rel <= S->tol) {
+    S->status = 0;
+    S->done = 1;
+    return true;
+  }
+  if (k >= S->maxit) {
+    S->status = 1;
+    S->done = 1;
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void breakdown(DevState* S) {
+  S->status = 2;
+  S->done = 1;
+}
+
+// alpha_k = nu_k / mu_k and, for the predict-and-recompute variants,
+// nu'_{k+1} (Eq. 2.3, or Meurant's form) and beta_{k+1} = nu'_{k+1} / nu_k.
+__device__ __forceinline__ void scalar_step_pr(DevState* S, bool meurant) {
+  const double nu = S->nu, mu = S->mu, sigma = S->sigma, gamma = S->gamma;
+  if (!finite(nu) || !finite(mu) || !(mu > 0.0) || nu < 0.0) { breakdown(S); return; }
+  const double alpha = nu / mu;
+  double nu_pred;
+  if (meurant) {
+    nu_pred = -nu + alpha * alpha * gamma;
+  } else {
+    nu_pred = nu - 2.0 * alpha * sigma + alpha * alpha * gamma;
+  }
+  if (!finite(nu_pred) || nu_pred < 0.0 || nu == 0.0) { breakdown(S); return; }
+  S->alpha = alpha;
+  S->nu_pred = nu_pred;
+  S->beta = nu_pred / nu;
+}
+
+}  // namespace prcg

@@ -1,0 +1,12 @@
+// Instantiation of the fused sweeps for CSR matrices.
+#include "prcg_launch.cuh"
+
+namespace prcg {
+
+LaunchFn launcher_csr(int op_kind, int pc_kind) {
+  if (op_kind == OP_CSR && pc_kind == PC_NONE) return &launch_phase<CsrOp, PcNone>;
+  if (op_kind == OP_CSR && pc_kind == PC_VEC) return &launch_phase<CsrOp, PcVec>;
+  return nullptr;
+}
+
+}  // namespace prcg

@@ -1,0 +1,106 @@
+// Host-side launch of the fused sweeps for one (operator, preconditioner)
+// pair.  Each prcg_inst_*.cu file instantiates this for its operator so the
+// library compiles in parallel translation units.
+#pragma once
+
+#include "prcg_kernels.cuh"
+
+namespace prcg {
+
+enum Phase {
+  PH_INIT_A = 0,
+  PH_INIT_B = 1,
+  PH_INIT_C = 2,
+  PH_HS_A = 3,
+  PH_HS_B = 4,
+  PH_PR = 5,
+  PH_PIPE = 6,
+  PH_TRUE_RES = 7
+};
+
+struct Plan {
+  OpDesc op;
+  PcDesc pc;
+  Vecs v;
+  DevState* S;
+  double* partials;
+  int sms;
+};
+
+using LaunchFn = cudaError_t (*)(const Plan&, int phase, int variant, int qr, int qw,
+                                 cudaStream_t);
+
+// CTAs for a sweep: enough to fill every SM at the kernel's occupancy, but
+// never more tiles than rows.
+template <class K>
+inline int grid_for(K kernel, int n, int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, 0) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  long tiles = ((long)n + kBlock - 1) / kBlock;
+  long g = (long)per_sm * sms;
+  if (g > tiles) g = tiles;
+  if (g > kMaxGrid) g = kMaxGrid;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+template <class Op, class Pc>
+cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, cudaStream_t st) {
+  Op op(P.op);
+  Pc pc(P.pc);
+  const int n = P.op.n;
+  const int meurant = (variant == V_M || variant == V_PIPE_M) ? 1 : 0;
+  switch (phase) {
+    case PH_INIT_A: {
+      auto k = k_init_a<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);
+      break;
+    }
+    case PH_INIT_B: {
+      auto k = k_init_b<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, variant);
+      break;
+    }
+    case PH_INIT_C: {
+      auto k = k_init_c<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S);
+      break;
+    }
+    case PH_HS_A: {
+      auto k = k_hs_a<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr);
+      break;
+    }
+    case PH_HS_B: {
+      auto k = k_hs_b<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw);
+      break;
+    }
+    case PH_PR: {
+      auto k = k_pr<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw, meurant);
+      break;
+    }
+    case PH_PIPE: {
+      auto k = k_pipe<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw, meurant);
+      break;
+    }
+    case PH_TRUE_RES: {
+      auto k = k_true_res<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);
+      break;
+    }
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Launchers exported by the instantiation units.
+cudaError_t launch_csr(const Plan&, int, int, int, int, cudaStream_t);
+LaunchFn launcher_for(int op_kind, int pc_kind);
+
+}  // namespace prcg

@@ -1,0 +1,174 @@
+// Operators (y_i = sum_j a_ij g(j)) and Jacobi preconditioners.
+//
+// Every fused sweep evaluates the matrix-vector product of a vector that is
+// itself being updated in the same sweep (Algorithm 2: s_k = A p_k with
+// p_k = r~_k + beta_k p_{k-1}).  The operators therefore take a gather
+// functor g(j) that returns the *new* value at column j, computed from the
+// previous iteration's vectors; the owner of row j computes the identical
+// expression, so the product uses exactly the stored p_k.
+#pragma once
+
+#include "prcg_common.cuh"
+
+namespace prcg {
+
+enum OpKind { OP_CSR = 0, OP_ST2 = 1, OP_ST3 = 2, OP_VC2 = 3, OP_VC3 = 4 };
+enum PcKind { PC_NONE = 0, PC_SCALAR = 1, PC_VEC = 2 };
+
+// Host-side description of an operator; the device structs below are built
+// from it.
+struct OpDesc {
+  int kind;
+  int n;
+  int nx, ny, nz;
+  const int* rp;
+  const int* ci;
+  const double* va;
+  const double* fx;
+  const double* fy;
+  const double* fz;
+  const double* adiag;   // variable-coefficient diagonal incl. shift
+  double cdiag;          // constant-coefficient diagonal 2*dim + shift
+};
+
+struct PcDesc {
+  int kind;
+  const double* d;
+  double dscalar;
+};
+
+// ---------------------------------------------------------------- CSR
+struct CsrOp {
+  const int* __restrict__ rp;
+  const int* __restrict__ ci;
+  const double* __restrict__ va;
+  int n;
+  explicit CsrOp(const OpDesc& o) : rp(o.rp), ci(o.ci), va(o.va), n(o.n) {}
+  template <class G>
+  __device__ __forceinline__ double row(int i, G&& g) const {
+    const int e0 = __ldg(rp + i), e1 = __ldg(rp + i + 1);
+    double acc = 0.0;
+    for (int e = e0; e < e1; ++e) acc = fma(__ldg(va + e), g(__ldg(ci + e)), acc);
+    return acc;
+  }
+  template <class G1, class G2>
+  __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
+    const int e0 = __ldg(rp + i), e1 = __ldg(rp + i + 1);
+    double c1 = 0.0, c2 = 0.0;
+    for (int e = e0; e < e1; ++e) {
+      const double a = __ldg(va + e);
+      const int j = __ldg(ci + e);
+      c1 = fma(a, g1(j), c1);
+      c2 = fma(a, g2(j), c2);
+    }
+    a1 = c1;
+    a2 = c2;
+  }
+};
+
+// ------------------------------------------- constant-coefficient stencil
+// 5-point (DIM 2) / 7-point (DIM 3) Poisson with Dirichlet-0 boundary:
+// y_i = cdiag * g(i) - sum over existing neighbours g(j).
+template <int DIM>
+struct StencilOp {
+  int nx, ny, nz, n;
+  double cdiag;
+  explicit StencilOp(const OpDesc& o) : nx(o.nx), ny(o.ny), nz(o.nz), n(o.n), cdiag(o.cdiag) {}
+  template <class F>
+  __device__ __forceinline__ void visit(int i, F&& f) const {
+    // f(j, coefficient) in increasing column order
+    const int x = i % nx;
+    const int yz = i / nx;
+    const int y = yz % ny;
+    const int z = yz / ny;
+    const int pl = nx * ny;
+    if (DIM == 3 && z > 0) f(i - pl, -1.0);
+    if (y > 0) f(i - nx, -1.0);
+    if (x > 0) f(i - 1, -1.0);
+    f(i, cdiag);
+    if (x < nx - 1) f(i + 1, -1.0);
+    if (y < ny - 1) f(i + nx, -1.0);
+    if (DIM == 3 && z < nz - 1) f(i + pl, -1.0);
+  }
+  template <class G>
+  __device__ __forceinline__ double row(int i, G&& g) const {
+    double acc = 0.0;
+    visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
+    return acc;
+  }
+  template <class G1, class G2>
+  __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
+    double c1 = 0.0, c2 = 0.0;
+    visit(i, [&](int j, double a) {
+      c1 = fma(a, g1(j), c1);
+      c2 = fma(a, g2(j), c2);
+    });
+    a1 = c1;
+    a2 = c2;
+  }
+};
+
+// ------------------------------------------- variable-coefficient stencil
+// A = sum_f c_f (e_a - e_b)(e_a - e_b)^T (+ shift I); diagonal precomputed.
+template <int DIM>
+struct VarStencilOp {
+  int nx, ny, nz, n;
+  const double* __restrict__ fx;
+  const double* __restrict__ fy;
+  const double* __restrict__ fz;
+  const double* __restrict__ adiag;
+  explicit VarStencilOp(const OpDesc& o)
+      : nx(o.nx), ny(o.ny), nz(o.nz), n(o.n), fx(o.fx), fy(o.fy), fz(o.fz), adiag(o.adiag) {}
+  template <class F>
+  __device__ __forceinline__ void visit(int i, F&& f) const {
+    const int x = i % nx;
+    const int yz = i / nx;
+    const int y = yz % ny;
+    const int z = yz / ny;
+    const int pl = nx * ny;
+    if (DIM == 3 && z > 0) f(i - pl, -__ldg(fz + i));
+    if (y > 0) f(i - nx, -__ldg(fy + (z * (ny + 1) + y) * nx + x));
+    if (x > 0) f(i - 1, -__ldg(fx + yz * (nx + 1) + x));
+    f(i, __ldg(adiag + i));
+    if (x < nx - 1) f(i + 1, -__ldg(fx + yz * (nx + 1) + x + 1));
+    if (y < ny - 1) f(i + nx, -__ldg(fy + (z * (ny + 1) + y + 1) * nx + x));
+    if (DIM == 3 && z < nz - 1) f(i + pl, -__ldg(fz + i + pl));
+  }
+  template <class G>
+  __device__ __forceinline__ double row(int i, G&& g) const {
+    double acc = 0.0;
+    visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
+    return acc;
+  }
+  template <class G1, class G2>
+  __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
+    double c1 = 0.0, c2 = 0.0;
+    visit(i, [&](int j, double a) {
+      c1 = fma(a, g1(j), c1);
+      c2 = fma(a, g2(j), c2);
+    });
+    a1 = c1;
+    a2 = c2;
+  }
+};
+
+// ------------------------------------------------------ preconditioners
+struct PcNone {
+  static constexpr bool on = false;
+  explicit PcNone(const PcDesc&) {}
+  __device__ __forceinline__ double operator()(int) const { return 1.0; }
+};
+struct PcScalar {
+  static constexpr bool on = true;
+  double d;
+  explicit PcScalar(const PcDesc& p) : d(p.dscalar) {}
+  __device__ __forceinline__ double operator()(int) const { return d; }
+};
+struct PcVec {
+  static constexpr bool on = true;
+  const double* __restrict__ d;
+  explicit PcVec(const PcDesc& p) : d(p.d) {}
+  __device__ __forceinline__ double operator()(int i) const { return __ldg(d + i); }
+};
+
+}  // namespace prcg

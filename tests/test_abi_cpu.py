@@ -1,0 +1,67 @@
+"""The C ABI library builds, loads without a GPU and exports every symbol
+include/*.h declares (no compute calls: this runs on CPU-only machines)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(prcg_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1905_01549_gb300 import binding
+    return binding.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert {"prcg_create_csr", "prcg_create_stencil", "prcg_solve", "prcg_destroy",
+            "prcg_last_error"} <= names
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_names_match_header(lib):
+    from paper_1905_01549_gb300 import binding
+    assert set(binding.EXPORTS) <= _declared()
+    for name in binding.EXPORTS:
+        assert callable(getattr(binding, name))
+
+
+def test_host_side_argument_checks_need_no_gpu(lib):
+    """Argument validation happens before any CUDA call."""
+    from paper_1905_01549_gb300 import binding
+    out = ctypes.c_void_p()
+    assert lib.prcg_create_stencil(ctypes.byref(out), 4, 8, 8, 8, None, 0.0, 0, None) == -1
+    assert b"dim" in lib.prcg_last_error(None)
+    assert lib.prcg_create_stencil(ctypes.byref(out), 3, 0, 8, 8, None, 0.0, 0, None) == -1
+    assert lib.prcg_create_stencil(ctypes.byref(out), 3, 8, 8, 8, None, -1.0, 0, None) == -1
+    assert lib.prcg_create_stencil(ctypes.byref(out), 3, 8, 8, 8, None, 0.0, 7, None) == -1
+    assert lib.prcg_create_csr(ctypes.byref(out), 0, 0, None, None, None, 0, None) == -1
+    assert lib.prcg_solve(None, 1, None, None, 1e-8, 10, None, None, None) == -1
+    assert lib.prcg_destroy(None) == 0
+    assert lib.prcg_n(None) == -1
+    with pytest.raises(binding.PrcgError):
+        binding.prcg_create_stencil(5, 4, 4, 4)
+
+
+def test_no_cpu_fallback_in_product_path():
+    """The package must not import the oracle (test infrastructure) anywhere."""
+    pkg = os.path.join(ROOT, "paper_1905_01549_gb300")
+    for f in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
+        src = open(f).read()
+        assert "import oracle" not in src and "from oracle" not in src, f

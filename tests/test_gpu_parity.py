@@ -1,0 +1,190 @@
+"""GPU (C ABI) vs CPU oracle, element by element on the same seeded inputs.
+
+Bar (from the method's statement of the target): FP64 iterates within 1e-10
+relative of the oracle over the first 20 iterations, the iteration count to
+the tolerance within 5 %, and the final true residual at the tolerance.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import CASES, GPU_VARIANTS, case, csr_matrix, make_solver, rel
+
+pytestmark = pytest.mark.gpu
+
+ITER_TOL = 1e-10     # relative, first 20 iterations
+HIST_TOL = 1e-9      # per entry of ||r_k|| / ||b||
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1905_01549_gb300 as G
+    return G
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    import torch
+    return torch
+
+
+def _oracle_d(A, precond):
+    return O.jacobi_inverse_diagonal(A) if precond == "jacobi" else None
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("op", ["csr", "stencil"])
+@pytest.mark.parametrize("precond", ["none", "jacobi"])
+def test_first_20_iterations(G, torch_mod, name, op, precond):
+    torch = torch_mod
+    prob = case(name)
+    A = csr_matrix(prob)
+    d = _oracle_d(A, precond)
+    b = torch.from_numpy(prob.b).cuda()
+    with make_solver(G, prob, op, precond) as S:
+        for variant in GPU_VARIANTS:
+            for k in (1, 2, 7, 20):
+                res = S.solve(b, variant=variant, tol=0.0, maxit=k, history=True)
+                ref = O.solve(variant, A, prob.b, d=d, tol=0.0, maxit=k)
+                assert res.status == ref.status == O.NOT_CONVERGED
+                assert res.iters == k
+                assert rel(res.x.cpu().numpy(), ref.x) <= ITER_TOL, (variant, k)
+                h = np.asarray(ref.hist)
+                assert np.all(np.abs(res.hist - h) <= HIST_TOL * h), (variant, k)
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("op", ["csr", "stencil"])
+@pytest.mark.parametrize("precond", ["none", "jacobi"])
+def test_converged_solve(G, torch_mod, name, op, precond):
+    torch = torch_mod
+    prob = case(name)
+    A = csr_matrix(prob)
+    d = _oracle_d(A, precond)
+    b = torch.from_numpy(prob.b).cuda()
+    tol = 1e-10
+    with make_solver(G, prob, op, precond) as S:
+        for variant in GPU_VARIANTS:
+            ref = O.solve(variant, A, prob.b, d=d, tol=tol, maxit=4 * prob.n)
+            res = S.solve(b, variant=variant, tol=tol, maxit=4 * prob.n, history=True,
+                          true_relres=True)
+            assert res.status == ref.status == O.OK, variant
+            assert abs(res.iters - ref.iters) <= max(1, 0.05 * ref.iters), (variant, res.iters, ref.iters)
+            assert res.hist[-1] <= tol
+            assert res.true_relres <= 20 * tol, (variant, res.true_relres)
+            assert rel(res.x.cpu().numpy(), ref.x) <= 1e-7, variant
+
+
+def test_nonzero_x0_and_host_pointers(G, torch_mod):
+    torch = torch_mod
+    prob = case("poisson3d_ragged")
+    A = csr_matrix(prob)
+    x0 = np.random.default_rng(4).standard_normal(prob.n)
+    with make_solver(G, prob, "csr", "jacobi") as S:
+        for variant in GPU_VARIANTS:
+            ref = O.solve(variant, A, prob.b, x0=x0.copy(), d=O.jacobi_inverse_diagonal(A),
+                          tol=0.0, maxit=15)
+            # host (numpy) b and x: the library copies in and out
+            xh = x0.copy()
+            res = S.solve(prob.b, x0=xh, variant=variant, tol=0.0, maxit=15)
+            assert res.x is xh and rel(xh, ref.x) <= ITER_TOL
+            # device tensors, x updated in place
+            xd = torch.from_numpy(x0.copy()).cuda()
+            res = S.solve(torch.from_numpy(prob.b).cuda(), x0=xd, variant=variant, tol=0.0, maxit=15)
+            assert rel(xd.cpu().numpy(), ref.x) <= ITER_TOL
+
+
+def test_edge_cases(G, torch_mod):
+    torch = torch_mod
+    prob = case("poisson2d_64")
+    A = csr_matrix(prob)
+    with make_solver(G, prob, "stencil", "none") as S:
+        for variant in GPU_VARIANTS:
+            # b = 0: x = 0, K = 0
+            x = torch.ones(prob.n, dtype=torch.float64, device="cuda")
+            res = S.solve(torch.zeros_like(x), x0=x, variant=variant, tol=1e-10, maxit=100)
+            assert res.status == G.PRCG_OK and res.iters == 0 and float(x.abs().max()) == 0.0
+            # x0 = exact solution of a system built from it: K = 0 at tol 1e-12
+            xt = torch.from_numpy(prob.x_true).cuda()
+            res = S.solve(torch.from_numpy(prob.b).cuda(), x0=xt.clone(), variant=variant,
+                          tol=1e-12, maxit=100, history=True)
+            assert res.iters == 0 and res.status == G.PRCG_OK
+            # maxit = 0 and a tiny maxit
+            res = S.solve(torch.from_numpy(prob.b).cuda(), variant=variant, tol=1e-10, maxit=0)
+            assert res.status == G.PRCG_NOT_CONVERGED and res.iters == 0
+            res = S.solve(torch.from_numpy(prob.b).cuda(), variant=variant, tol=1e-10, maxit=3)
+            assert res.status == G.PRCG_NOT_CONVERGED and res.iters == 3
+
+
+def test_n_equals_one_and_one_tile(G, torch_mod):
+    torch = torch_mod
+    import problems as P
+    for dims in [(1, 1), (16, 16), (1, 1, 1), (256, 1), (257, 1)]:
+        prob = P.grid_problem(dims, "t_small")
+        A = csr_matrix(prob)
+        for op in ("csr", "stencil"):
+            with make_solver(G, prob, op, "jacobi") as S:
+                for variant in GPU_VARIANTS:
+                    ref = O.solve(variant, A, prob.b, d=O.jacobi_inverse_diagonal(A), tol=1e-12,
+                                  maxit=4 * prob.n + 4)
+                    res = S.solve(torch.from_numpy(prob.b).cuda(), variant=variant, tol=1e-12,
+                                  maxit=4 * prob.n + 4)
+                    assert res.status == ref.status and abs(res.iters - ref.iters) <= 1, (dims, op, variant)
+                    assert rel(res.x.cpu().numpy(), ref.x) <= 1e-9
+
+
+def test_breakdown_on_indefinite_matrix(G, torch_mod):
+    """An indefinite symmetric A: the oracle and the GPU stop with BREAKDOWN at
+    the same iteration (mu <= 0 or nu' < 0, Section 3.1)."""
+    torch = torch_mod
+    import scipy.sparse as sp
+    n = 300
+    rng = np.random.default_rng(8)
+    diag = rng.uniform(1.0, 2.0, n)
+    diag[::7] *= -1.0
+    A = sp.diags([np.full(n - 1, 0.3), diag, np.full(n - 1, 0.3)], [-1, 0, 1], format="csr")
+    b = rng.standard_normal(n)
+    with G.Solver.from_csr(A.indptr, A.indices, A.data) as S:
+        for variant in GPU_VARIANTS:
+            ref = O.solve(variant, A, b, tol=1e-12, maxit=2000)
+            res = S.solve(torch.from_numpy(b).cuda(), variant=variant, tol=1e-12, maxit=2000)
+            assert ref.status == O.BREAKDOWN
+            assert res.status == G.PRCG_BREAKDOWN and res.iters == ref.iters, (variant, res.iters, ref.iters)
+
+
+def test_invalid_inputs_are_rejected(G):
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([0, 5], dtype=np.int32)        # column out of range
+    v = np.array([1.0, 1.0])
+    with pytest.raises(G.PrcgError):
+        G.Solver.from_csr(rp, ci, v)
+    ci = np.array([1, 0], dtype=np.int32)        # no diagonal: Jacobi impossible
+    with pytest.raises(G.PrcgError):
+        G.Solver.from_csr(rp, ci, v, precond="jacobi")
+    rp_bad = np.array([0, 2, 1], dtype=np.int32)  # decreasing row_ptr
+    with pytest.raises(G.PrcgError):
+        G.Solver.from_csr(rp_bad, np.array([0, 1], dtype=np.int32), v)
+    S = G.Solver.from_stencil((8, 8))
+    with pytest.raises(G.PrcgError):
+        S.solve(np.ones(64), variant="pr", tol=-1.0)
+    with pytest.raises(G.PrcgError):
+        S.solve(np.ones(64), variant="gv", tol=1e-8)
+    S.close()
+
+
+def test_reruns_are_bitwise_identical(G, torch_mod):
+    """Fixed-order reductions: the same solve twice gives identical bits."""
+    torch = torch_mod
+    prob = case("varcoef3d_ragged")
+    b = torch.from_numpy(prob.b).cuda()
+    with make_solver(G, prob, "csr", "jacobi") as S:
+        for variant in GPU_VARIANTS:
+            r1 = S.solve(b, variant=variant, tol=1e-10, maxit=5000, history=True)
+            r2 = S.solve(b, variant=variant, tol=1e-10, maxit=5000, history=True)
+            assert r1.iters == r2.iters
+            assert torch.equal(r1.x, r2.x) and np.array_equal(r1.hist, r2.hist)
