@@ -178,13 +178,15 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   CK(cudaEventCreate(&c->ev_start));
   CK(cudaEventCreate(&c->ev_init));
   CK(cudaEventCreate(&c->ev_loop));
-  // 17 n-vectors: x, b, t, d and two buffers each of r, r~, p, s, s~, w, u
-  const size_t nv = 17;
+  // 18 n-vectors: x, b, t, d and two buffers each of r, r~, p, s, s~, w, u
+  const size_t nv = 18;
   CK(cudaMalloc(&c->pool, nv * (size_t)n * sizeof(double)));
   double* q = c->pool;
+  size_t taken = 0;
   auto take = [&]() {
     double* r = q;
     q += n;
+    ++taken;
     return r;
   };
   Vecs& V = c->plan.v;
@@ -202,6 +204,7 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
     V.u[k] = take();
   }
   c->plan.pc.d = d;
+  if (taken != nv) return set_err(c, PRCG_ERR_INVALID, "internal: vector pool size mismatch");
   CK(cudaMalloc(&c->partials, (size_t)kMaxGrid * kMaxNV * sizeof(double)));
   CK(cudaMalloc(&c->S, sizeof(DevState)));
   CK(cudaMemset(c->S, 0, sizeof(DevState)));
