@@ -155,6 +155,37 @@ const char* prcg_last_error(const prcg_ctx* ctx);
 /* prcg_n -- the number of unknowns of the context (or -1 for NULL). */
 int64_t prcg_n(const prcg_ctx* ctx);
 
+/*
+ * prcg_pr_solve_stencil_noalloc -- PR-CG on a small constant-coefficient
+ * stencil system without any device allocation.  The paper has no
+ * counterpart: this is a deployment form of the PR-CG sweep for callers that
+ * cannot allocate device memory -- code running under another framework's
+ * memory pool or allocator hooks, real-time loops that forbid cudaMalloc /
+ * cudaFree after start-up, and callers that cannot keep a context alive.
+ *
+ * The operator is the one of prcg_create_stencil with face_coeff == NULL
+ * (diagonal 2*dim + diag_shift, off-diagonal -1, Dirichlet-0).  The whole
+ * solve runs as one single-CTA kernel; the iteration vectors live in a
+ * file-scope device array of fixed size, allocated when the library is
+ * loaded and kept by every GPU that loads it until the process exits:
+ * n = nx*ny*nz must be <= 65536 (the array holds 8 vectors of 65536 doubles,
+ * 4 MiB).  Larger n returns PRCG_ERR_INVALID.
+ *   b, x              device pointers the caller owns (x: in x_0, out x_K)
+ *   residual_history  NULL or device double[maxit + 1]
+ *   iters_out         NULL or receives K
+ *   cuda_stream       stream to run on (NULL: legacy default stream)
+ * Returns PRCG_OK / PRCG_NOT_CONVERGED / PRCG_BREAKDOWN or a negative error.
+ * Blocks until the result is known.  The first call on each device looks up
+ * the array's device address (cudaGetSymbolAddress): make that first call
+ * before any stream capture.  All calls share the one array, so calls that
+ * overlap on the GPU (other streams or host threads) race with each other
+ * and must be serialised by the caller.
+ */
+int prcg_pr_solve_stencil_noalloc(int dim, int64_t nx, int64_t ny, int64_t nz,
+                                  double diag_shift, int precond, const double* b, double* x,
+                                  double tol, int maxit, double* residual_history,
+                                  int* iters_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

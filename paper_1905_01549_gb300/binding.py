@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_INVALID", 
 
 # every symbol include/prcg.h declares
 EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_solve", "prcg_last_timing",
-           "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n")
+           "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n",
+           "prcg_pr_solve_stencil_noalloc")
 
 
 class PrcgError(RuntimeError):
@@ -74,6 +75,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.prcg_last_error.restype = ctypes.c_char_p
     lib.prcg_n.argtypes = [vp]
     lib.prcg_n.restype = ctypes.c_int64
+    lib.prcg_pr_solve_stencil_noalloc.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                                  ctypes.c_int64, ctypes.c_double, ctypes.c_int,
+                                                  vp, vp, ctypes.c_double, ctypes.c_int, vp,
+                                                  _c_int_p, vp]
+    lib.prcg_pr_solve_stencil_noalloc.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -167,3 +173,17 @@ def prcg_last_error(ctx=None) -> str:
 
 def prcg_n(ctx) -> int:
     return int(load().prcg_n(ctx))
+
+
+def prcg_pr_solve_stencil_noalloc(dim, nx, ny, nz, diag_shift, precond, b, x, tol, maxit,
+                                  residual_history=None, stream=None):
+    """PR-CG without device allocation (n <= 65536, device b / x);
+    returns (status, iters).  Raises PrcgError on a negative status."""
+    iters = ctypes.c_int(0)
+    rc = load().prcg_pr_solve_stencil_noalloc(int(dim), int(nx), int(ny), int(nz),
+                                              float(diag_shift), int(precond), ptr(b), ptr(x),
+                                              float(tol), int(maxit), ptr(residual_history),
+                                              ctypes.byref(iters), _stream_ptr(stream))
+    if rc < 0:
+        raise PrcgError(rc, "prcg_pr_solve_stencil_noalloc failed")
+    return rc, iters.value
