@@ -45,16 +45,17 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# --------------------------------------------------------------------------- bytes model
+# --------------------------------------------------------------------------- models
 def model_bytes(variant: str, op: str, precond: str, n: int, nnz: int, dim: int = 3) -> float:
-    """Algorithmic DRAM bytes of one iteration (all sweeps of it).
+    """Algorithmic DRAM bytes of one iteration, the fully fused minimum of the
+    method (every vector read and written once per iteration, A read once).
 
     V = 8n bytes per vector sweep.  A = 12 nnz + 4 (n+1) for CSR, 0 for the
     constant stencil, ~(dim + 1) V for the variable-coefficient stencil (face
-    arrays + diagonal).  Sweeps read / write:
-      HS:   A: R x p r s  W x r      B: R r p  W p s  (+A)       -> 10V + A
-      PR:   R x p r s  W x r p s (+A)                              ->  8V + A
-      pipe: R x p r s w u  W x r p s w u (+A, one pass)            -> 12V + A
+    arrays + diagonal).
+      HS:   R x p r s, W x r; R r p, W p s (+A)       -> 10V + A
+      PR:   R x p r s, W x r p s (+A)                  ->  8V + A
+      pipe: R x p r s w u, W x r p s w u (+A)          -> 12V + A
     Jacobi adds r~ (PR, pipe) and s~ (pipe) read+write, and one read of d per
     sweep when d is a vector (CSR, variable coefficients).
     """
@@ -74,6 +75,80 @@ def model_bytes(variant: str, op: str, precond: str, n: int, nnz: int, dim: int 
     if variant in ("pipe_pr", "pipe_m"):
         return 12 * V + A + (4 * V if jac else 0.0) + (V if dvec else 0.0)
     raise KeyError(variant)
+
+
+def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int):
+    """Per sweep of this library's schedule: (name, DRAM bytes the sweep must
+    move, FP64 instructions it must execute), counted per row and x n.
+
+    FP64 instructions are those of the algorithm (one FMA per stored matrix
+    entry, one FMA per vector update and per inner-product term, one multiply
+    per use of an explicit M^{-1} v); a 7-point stencil row counts 7.
+    """
+    V = 8.0 * n
+    A = 12.0 * nnz + 4.0 * (n + 1) if op == "csr" else 0.0
+    m = float(nnz) if op == "csr" else 7.0 * n
+    dv = 1.0 if (precond == "jacobi" and op == "csr") else 0.0   # read of vector d
+    jac = precond == "jacobi"
+    if variant == "hs":
+        return [("k_hs_a", (6 + dv) * V, (5 if jac and dv else 3) * n),
+                ("k_hs_b", (3 + dv) * V, (2 if jac else 1) * n),
+                ("k_hs_c", 2 * V + A, m + n)]
+    if variant in ("pr", "m"):
+        if jac:
+            return [("k_pr_a", (9 + dv) * V, 7 * n),
+                    ("k_pr_b", (3 + dv) * V + A, m + (4 if dv else 3) * n)]
+        return [("k_pr_a", 7 * V, 4 * n), ("k_pr_b", 3 * V + A, m + 3 * n)]
+    if variant in ("pipe_pr", "pipe_m"):
+        if jac:
+            return [("k_pipe", (12 + dv) * V + A, 2 * m + 15 * n)]
+        return [("k_pipe", 8 * V + A, 2 * m + 9 * n)]
+    raise KeyError(variant)
+
+
+FP64_PER_SM_CLK = 2.0   # DFMA issue rate of a GB300 SM (ncu: sm__sass_thread_inst_executed_op_dfma peak)
+N_SMS = 152
+
+
+def fp64_peak(sm_mhz=None) -> float:
+    """FP64 instructions/s of the whole GPU at the given (or maximum) SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mx = float(json.load(f).get("sm_max_mhz", 2070.0))
+    except Exception:
+        mx = 2070.0
+    clk = sm_mhz if sm_mhz else mx
+    return FP64_PER_SM_CLK * N_SMS * clk * 1e6
+
+
+def sweep_roofline(S, variant, op, precond, n, nnz, reps=20, sm_mhz=None):
+    """Time every sweep of one iteration with CUDA events (prcg_time_sweeps)
+    and place the slowest one on both rooflines (HBM bytes, FP64 issue)."""
+    from paper_1905_01549_gb300 import binding
+    ms = binding.prcg_time_sweeps(S.handle, binding.VARIANT_IDS[variant], reps)
+    models = sweep_models(variant, op, precond, n, nnz)
+    peak_hbm, hbm_src = _peaks()
+    peak_fp = fp64_peak(sm_mhz)
+    per = []
+    for (name, by, fp), t in zip(models, ms):
+        ts = t / 1e3
+        per.append({"kernel": name, "us": t * 1e3, "model_bytes": by, "model_fp64": fp,
+                    "hbm_frac": by / ts / 1e9 / peak_hbm, "alu_frac": fp / ts / peak_fp})
+    dom = max(range(len(per)), key=lambda q: per[q]["us"])
+    d = per[dom]
+    t_hbm = d["model_bytes"] / (peak_hbm * 1e9)
+    t_alu = d["model_fp64"] / peak_fp
+    if t_alu > t_hbm:
+        roof = {"bound": "alu", "achieved": d["model_fp64"] / (d["us"] / 1e6) / 1e9,
+                "peak": peak_fp / 1e9, "unit": "G FP64-inst/s", "frac": d["alu_frac"],
+                "peak_source": "derived: 2 FP64 inst/clk/SM x 152 SMs x SM clock"}
+    else:
+        roof = {"bound": "hbm", "achieved": d["model_bytes"] / (d["us"] / 1e6) / 1e9,
+                "peak": peak_hbm, "unit": "GB/s", "frac": d["hbm_frac"], "peak_source": hbm_src}
+    roof.update({"kernel": d["kernel"], "launch_us": d["us"], "bytes_per_launch": d["model_bytes"],
+                 "fp64_per_launch": d["model_fp64"], "hbm_frac": d["hbm_frac"],
+                 "alu_frac": d["alu_frac"], "sweeps": per})
+    return roof
 
 
 # --------------------------------------------------------------------------- clocks
@@ -129,8 +204,6 @@ class ClockSampler:
 # --------------------------------------------------------------------------- workloads
 def build_problem(name: str):
     import problems as P
-    if name.startswith("poisson3d_256"):
-        return P.poisson3d(256)
     if name.startswith("poisson3d_"):
         return P.poisson3d(int(name.split("_")[1]))
     if name.startswith("varcoef3d_128"):
@@ -206,11 +279,11 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    wl = args.workload
-    prob = build_problem(wl)
+    prob = build_problem(args.workload)
+    wl = f"{args.workload}_{args.op}_{args.precond}_{args.variant}"
     n = prob.n
-    nnz = len(prob.csr[2]) if prob.csr is not None else 0
-    op, precond, variant, tol = "csr", "jacobi", "pr", 1e-10
+    nnz = len(prob.csr[2]) if (prob.csr is not None and args.op == "csr") else 0
+    op, precond, variant, tol = args.op, args.precond, args.variant, 1e-10
     maxit = 20000
     b_dev = torch.from_numpy(prob.b).cuda()
     S = make_solver(G, prob, op, precond)
@@ -233,10 +306,10 @@ def run_ours(args):
         dev_s_max, all_iters = dev_s, float(tot_iters)
     value = all_iters / dev_s_max
     K = main["iters"][-1]
-    peak, peak_kind = _peaks()
+    clocks = clk.summary()
+    roof = sweep_roofline(S, variant, op, precond, n, nnz, sm_mhz=clocks.get("sm_mhz"))
+    roof["traffic"] = ncu_traffic(f"{roof['kernel']}@{wl}")
     bytes_it = model_bytes(variant, op, precond, n, nnz)
-    per_launch_s = main["loop_ms"] / 1e3 / max(K, 1)
-    achieved = bytes_it / per_launch_s / 1e9
     line = {
         "metric": METRIC,
         "value": value,
@@ -255,14 +328,12 @@ def run_ours(args):
                    "step": "one complete solve to tol on resident inputs",
                    "l2": "inputs larger than L2 (CSR %.2f GB + vectors)" % ((12 * nnz + 4 * n) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "peak_source": peak_kind,
-                     "kernel": "k_pr<CsrOp,PcVec>",
-                     "bytes_per_launch": bytes_it,
-                     "launch_us": per_launch_s * 1e6,
-                     "traffic": ncu_traffic("k_pr<CsrOp,PcVec>@poisson3d_256")},
+        "roofline": roof,
+        "iteration": {"us": main["loop_ms"] * 1e3 / max(K, 1),
+                      "algorithmic_bytes": bytes_it,
+                      "hbm_gbs": bytes_it / (main["loop_ms"] / 1e3 / max(K, 1)) / 1e9},
         "gpu_launches": main["launches"],
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     if rank == 0 and not args.no_extras:
         line["e2e"] = run_e2e(G, S, prob, variant, tol, maxit, args)
@@ -314,11 +385,12 @@ def run_variants(G, prob, S_main, b_dev, args):
             K = r["iters"][-1]
             per = r["loop_ms"] / 1e3 / K
             by = model_bytes(variant, op, "jacobi", n, nnz)
+            rf = sweep_roofline(S, variant, op, "jacobi", n, nnz if op == "csr" else 0)
             out[f"{op}/jacobi/{variant}"] = {
                 "iters_per_s": sum(r["iters"]) / (sum(r["dev_ms"]) / 1e3), "iters": K,
-                "us_per_iter": per * 1e6, "model_gb_per_iter": by / 1e9,
-                "achieved_gbs": by / per / 1e9, "frac": by / per / 1e9 / peak,
-                "status": r["status"]}
+                "us_per_iter": per * 1e6, "algorithmic_gb_per_iter": by / 1e9,
+                "algorithmic_gbs": by / per / 1e9, "algorithmic_hbm_frac": by / per / 1e9 / peak,
+                "sweeps": rf["sweeps"], "status": r["status"]}
         if op != "csr":
             S.close()
     # variable-coefficient diffusion 128^3, sigma = 2, Jacobi
@@ -390,7 +462,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": args.workload, "n": prob.n, "nnz": len(v), "operator": "csr",
+            "config": {"workload": f"{args.workload}_csr_jacobi_pr", "n": prob.n, "nnz": len(v),
+                       "operator": "csr",
                        "precond": "jacobi", "variant": "pr", "tol": 1e-10},
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
                              "sample": f"each step: oracle PR-CG initialisation + {per} iterations "
@@ -406,8 +479,12 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="poisson3d_256_csr_jacobi_pr")
+    ap.add_argument("--workload", default="poisson3d_256",
+                    help="problem: poisson3d_256, poisson3d_<N>, varcoef3d_128")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--op", default="csr", choices=["csr", "stencil"])
+    ap.add_argument("--variant", default="pr", choices=["pr", "hs", "pipe_pr", "m", "pipe_m"])
+    ap.add_argument("--precond", default="jacobi", choices=["jacobi", "none"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

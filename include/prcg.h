@@ -136,6 +136,20 @@ int prcg_solve(prcg_ctx* ctx, int variant, const double* b, double* x,
 int prcg_last_timing(const prcg_ctx* ctx, float* init_ms, float* loop_ms, int* iters);
 
 /*
+ * prcg_time_sweeps -- average device time of each sweep (kernel) of one
+ * iteration of `variant`, from CUDA events recorded around every launch on
+ * the context's stream.  Runs initialize() and then `reps` iterations for
+ * b = 1, x_0 = 0, with the stopping and breakdown tests switched off (the
+ * sweeps always do their full work), and leaves the context's vectors in an
+ * unspecified state (the next prcg_solve copies its own b and x_0 in).
+ *   ms_per_sweep  float[3]: HS: sweeps A (x, r), B (p), C (s = A p);
+ *                 PR / M: A (x, r, r~, p), B (s = A p and the inner products);
+ *                 pipe-PR / pipe-M: the single sweep
+ *   nsweeps       receives the number of sweeps written (3, 2 or 1)
+ */
+int prcg_time_sweeps(prcg_ctx* ctx, int variant, int reps, float* ms_per_sweep, int* nsweeps);
+
+/*
  * prcg_last_launches -- number of this library's kernels the last
  * prcg_solve launched (initialisation sweeps, iteration sweeps including the
  * no-op sweeps after convergence within the last loop body, loop-control

@@ -29,6 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_INVALID", 
 
 # every symbol include/prcg.h declares
 EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_solve", "prcg_last_timing",
+           "prcg_time_sweeps",
            "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n",
            "prcg_pr_solve_stencil_noalloc")
 
@@ -67,6 +68,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.prcg_solve.restype = ctypes.c_int
     lib.prcg_last_timing.argtypes = [vp, _c_float_p, _c_float_p, _c_int_p]
     lib.prcg_last_timing.restype = ctypes.c_int
+    lib.prcg_time_sweeps.argtypes = [vp, ctypes.c_int, ctypes.c_int, _c_float_p, _c_int_p]
+    lib.prcg_time_sweeps.restype = ctypes.c_int
     lib.prcg_last_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.prcg_last_launches.restype = ctypes.c_int
     lib.prcg_destroy.argtypes = [vp]
@@ -154,6 +157,14 @@ def prcg_last_timing(ctx):
     a, b, k = ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
     _check(lib.prcg_last_timing(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)), ctx)
     return a.value, b.value, k.value
+
+
+def prcg_time_sweeps(ctx, variant, reps):
+    """Average ms of each sweep of one iteration (list of 1 to 3 floats)."""
+    buf = (ctypes.c_float * 3)()
+    k = ctypes.c_int()
+    _check(load().prcg_time_sweeps(ctx, int(variant), int(reps), buf, ctypes.byref(k)), ctx)
+    return [buf[i] for i in range(k.value)]
 
 
 def prcg_last_launches(ctx) -> int:

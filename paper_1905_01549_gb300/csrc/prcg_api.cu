@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "../../include/prcg.h"
 #include "prcg_launch.cuh"
@@ -24,7 +25,7 @@ LaunchFn launcher_st(int op_kind, int pc_kind);
 LaunchFn launcher_vc(int op_kind, int pc_kind);
 
 LaunchFn launcher_for(int op_kind, int pc_kind) {
-  if (op_kind == OP_CSR) return launcher_csr(op_kind, pc_kind);
+  if (op_kind == OP_CSR || op_kind == OP_SELL) return launcher_csr(op_kind, pc_kind);
   if (op_kind == OP_ST2 || op_kind == OP_ST3) return launcher_st(op_kind, pc_kind);
   return launcher_vc(op_kind, pc_kind);
 }
@@ -60,6 +61,44 @@ __global__ void k_csr_jacobi(const int* rp, const int* ci, const double* va, int
   }
 }
 
+// SELL-32 conversion: entries per row of each 32-row slice (the slice max).
+__global__ void k_sell_len(const int* rp, int n, int nslices, int* slen) {
+  for (int sl = blockIdx.x * blockDim.x + threadIdx.x; sl < nslices; sl += gridDim.x * blockDim.x) {
+    int L = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int i = sl * 32 + l;
+      if (i < n) L = max(L, rp[i + 1] - rp[i]);
+    }
+    slen[sl] = L;
+  }
+}
+
+// SELL-32 fill: entry t of row i goes to sptr[i/32] + 32 t + i%32; padding
+// entries (and the rows past n in the last slice) point at a valid column
+// with value 0.
+__global__ void k_sell_fill(const int* rp, const int* ci, const double* va, int n, int nslices,
+                            const int* sptr, const int* slen, int* scol, double* sval) {
+  const int total = nslices * 32;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const int sl = i >> 5, l = i & 31;
+    const int L = slen[sl];
+    const int base = sptr[sl] + l;
+    const int e0 = i < n ? rp[i] : 0;
+    const int len = i < n ? rp[i + 1] - e0 : 0;
+    const int pad_col = i < n ? i : n - 1;
+    for (int t = 0; t < L; ++t) {
+      const int e = base + 32 * t;
+      if (t < len) {
+        scol[e] = ci[e0 + t];
+        sval[e] = va[e0 + t];
+      } else {
+        scol[e] = pad_col;
+        sval[e] = 0.0;
+      }
+    }
+  }
+}
+
 // Diagonal of the variable-coefficient operator: the sum of the cell's face
 // coefficients (x-, x+, y-, y+, z-, z+) plus the shift; optionally 1 / a_ii.
 __global__ void k_vc_diag(int dim, int nx, int ny, int nz, const double* fx, const double* fy,
@@ -85,6 +124,10 @@ __global__ void k_vc_diag(int dim, int nx, int ny, int nz, const double* fx, con
       }
     }
   }
+}
+
+__global__ void k_fill(double* v, int n, double a) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = a;
 }
 
 // Body-end control of the device-side while loop.
@@ -129,6 +172,8 @@ struct prcg_ctx {
   double* pool = nullptr;        // all n-length vectors
   int* ipool = nullptr;          // CSR indices
   double* vpool = nullptr;       // CSR values / faces / diagonals
+  int* sell_i = nullptr;         // SELL-32 slice pointers, lengths, columns
+  double* sell_v = nullptr;      // SELL-32 values
   double* partials = nullptr;
   DevState* S = nullptr;
   DevState* hS = nullptr;        // pinned mirror
@@ -205,7 +250,7 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   }
   c->plan.pc.d = d;
   if (taken != nv) return set_err(c, PRCG_ERR_INVALID, "internal: vector pool size mismatch");
-  CK(cudaMalloc(&c->partials, (size_t)kMaxGrid * kMaxNV * sizeof(double)));
+  CK(cudaMalloc(&c->partials, (size_t)kMaxGrid * (kMaxNV + 2) * sizeof(double)));
   CK(cudaMalloc(&c->S, sizeof(DevState)));
   CK(cudaMemset(c->S, 0, sizeof(DevState)));
   CK(cudaMallocHost(&c->hS, sizeof(DevState)));
@@ -213,6 +258,7 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   CK(cudaMemset(c->dbad, 0, sizeof(int)));
   c->plan.S = c->S;
   c->plan.partials = c->partials;
+  c->plan.partials_a = c->partials + (size_t)kMaxGrid * kMaxNV;
   const char* ng = getenv("PRCG_NO_GRAPH");
   c->use_graph = !(ng && ng[0] == '1');
   return PRCG_OK;
@@ -247,23 +293,36 @@ void destroy_graphs(prcg_ctx* c) {
 }
 
 int launch_init(prcg_ctx* c, int variant, cudaStream_t st) {
-  const bool pipe = variant == V_PIPE || variant == V_PIPE_M || variant == V_GV;
   CK(c->launch(c->plan, PH_INIT_A, variant, 0, 0, st));
   CK(c->launch(c->plan, PH_INIT_B, variant, 0, 0, st));
-  if (pipe) CK(c->launch(c->plan, PH_INIT_C, variant, 0, 0, st));
   return PRCG_OK;
 }
 
-// One iteration of `variant` reading buffer qr and writing buffer qw.
+int init_launches(int) { return 2; }
+
+// Kernels of one iteration of `variant`.
+int iter_launches(int variant) {
+  switch (variant) {
+    case V_HS: return 3;
+    case V_PR:
+    case V_M: return 2;
+    default: return 1;
+  }
+}
+
+// One iteration of `variant`; the pipelined sweep reads buffer qr and
+// writes buffer qw.
 int launch_iter(prcg_ctx* c, int variant, int qr, int qw, cudaStream_t st) {
   switch (variant) {
     case V_HS:
       CK(c->launch(c->plan, PH_HS_A, variant, qr, qw, st));
       CK(c->launch(c->plan, PH_HS_B, variant, qr, qw, st));
+      CK(c->launch(c->plan, PH_HS_C, variant, qr, qw, st));
       break;
     case V_PR:
     case V_M:
-      CK(c->launch(c->plan, PH_PR, variant, qr, qw, st));
+      CK(c->launch(c->plan, PH_PR_A, variant, qr, qw, st));
+      CK(c->launch(c->plan, PH_PR_B, variant, qr, qw, st));
       break;
     case V_PIPE:
     case V_PIPE_M:
@@ -363,10 +422,58 @@ int run_host_loop(prcg_ctx* c, int variant, int maxit) {
     for (int m = 0; m < chunk; ++m) {
       rc = launch_iter(c, variant, m & 1, (m + 1) & 1, c->cs);
       if (rc != PRCG_OK) return rc;
-      c->host_loop_launches += variant == V_HS ? 2 : 1;
+      c->host_loop_launches += iter_launches(variant);
     }
   }
   CK(cudaEventRecord(c->ev_loop, c->cs));
+  return PRCG_OK;
+}
+
+// Re-lay the validated CSR matrix out as SELL-32 (padding at most doubles
+// the stored entries; otherwise the CSR layout is kept).
+int build_sell(prcg_ctx* c) {
+  OpDesc& op = c->plan.op;
+  const int n = op.n;
+  const int nslices = (n + 31) / 32;
+  int* slen_d = nullptr;
+  CK(cudaMalloc(&slen_d, (size_t)nslices * sizeof(int)));
+  k_sell_len<<<c->plan.sms * 4, 256, 0, c->cs>>>(op.rp, n, nslices, slen_d);
+  std::vector<int> slen(nslices);
+  cudaError_t e = cudaMemcpyAsync(slen.data(), slen_d, (size_t)nslices * sizeof(int),
+                                  cudaMemcpyDeviceToHost, c->cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->cs);
+  cudaFree(slen_d);
+  if (e != cudaSuccess) return cuda_err(c, e, "SELL lengths");
+  std::vector<int> sptr(nslices + 1);
+  int64_t total = 0;
+  for (int sl = 0; sl < nslices; ++sl) {
+    sptr[sl] = (int)total;
+    total += 32 * (int64_t)slen[sl];
+    if (total >= ((int64_t)1 << 31) - 64) return PRCG_OK;  // keep CSR
+  }
+  sptr[nslices] = (int)total;
+  int nnz = 0;
+  CK(cudaMemcpy(&nnz, op.rp + n, sizeof(int), cudaMemcpyDeviceToHost));
+  if (total > 2 * (int64_t)nnz + 64 * (int64_t)nslices) return PRCG_OK;  // too much padding
+  const size_t ni = (size_t)(nslices + 1) + (size_t)nslices + (size_t)total + 4;
+  CK(cudaMalloc(&c->sell_i, ni * sizeof(int)));
+  CK(cudaMalloc(&c->sell_v, ((size_t)total + 2) * sizeof(double)));
+  int* sptr_d = c->sell_i;
+  int* slen2_d = c->sell_i + nslices + 1;
+  int* scol_d = slen2_d + nslices;
+  CK(cudaMemcpyAsync(sptr_d, sptr.data(), (size_t)(nslices + 1) * sizeof(int),
+                     cudaMemcpyHostToDevice, c->cs));
+  CK(cudaMemcpyAsync(slen2_d, slen.data(), (size_t)nslices * sizeof(int), cudaMemcpyHostToDevice,
+                     c->cs));
+  k_sell_fill<<<c->plan.sms * 8, 256, 0, c->cs>>>(op.rp, op.ci, op.va, n, nslices, sptr_d, slen2_d,
+                                                 scol_d, c->sell_v);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(c->cs));
+  op.sptr = sptr_d;
+  op.slen = slen2_d;
+  op.scol = scol_d;
+  op.sval = c->sell_v;
+  op.kind = OP_SELL;
   return PRCG_OK;
 }
 
@@ -434,6 +541,10 @@ int prcg_create_csr(prcg_ctx** out, int64_t n, int64_t nnz, const int32_t* row_p
     k_csr_jacobi<<<c->plan.sms * 4, 256, 0, c->cs>>>(rp, ci, va, (int)n,
                                                     const_cast<double*>(c->plan.pc.d), c->dbad);
     if ((rc = check_bad(c, "Jacobi needs a positive diagonal")) != PRCG_OK) return fail(rc);
+  }
+  const char* ns = getenv("PRCG_NO_SELL");
+  if (!(ns && ns[0] == '1')) {
+    if ((rc = build_sell(c)) != PRCG_OK) return fail(rc);
   }
   c->launch = launcher_for(c->plan.op.kind, c->plan.pc.kind);
   if (!c->launch) return fail(set_err(c, PRCG_ERR_UNSUPPORTED, "operator not built"));
@@ -546,9 +657,8 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   CK(cudaStreamSynchronize(c->cs));
   const int K = h.k;
   {
-    const bool pipe = variant == V_PIPE || variant == V_PIPE_M;
-    const int64_t per_iter = variant == V_HS ? 2 : 1;
-    int64_t launches = pipe ? 3 : 2;
+    const int64_t per_iter = iter_launches(variant);
+    int64_t launches = init_launches(variant);
     if (graph)
       launches += (int64_t)h.bodies * (chunk * per_iter + 1);
     else
@@ -590,6 +700,58 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   return status;
 }
 
+int prcg_time_sweeps(prcg_ctx* c, int variant, int reps, float* ms_per_sweep, int* nsweeps) {
+  if (!c || !ms_per_sweep || !nsweeps || reps < 1) return set_err(c, PRCG_ERR_INVALID, "bad argument");
+  if (variant < 0 || variant > 4) return set_err(c, PRCG_ERR_UNSUPPORTED, "variant not built");
+  int phases[3];
+  int np = 0;
+  if (variant == V_HS) {
+    phases[0] = PH_HS_A; phases[1] = PH_HS_B; phases[2] = PH_HS_C; np = 3;
+  } else if (variant == V_PR || variant == V_M) {
+    phases[0] = PH_PR_A; phases[1] = PH_PR_B; np = 2;
+  } else {
+    phases[0] = PH_PIPE; np = 1;
+  }
+  cudaEvent_t ev[4];
+  for (int q = 0; q <= np; ++q) CK(cudaEventCreate(&ev[q]));
+  // b = 1, x_0 = 0 (any right-hand side does the same work)
+  int rc = PRCG_OK;
+  DevState& h = *c->hS;
+  memset(&h, 0, sizeof h);
+  h.tol = 0.0;
+  h.maxit = 1 << 30;
+  h.status = kRunning;
+  h.profile = 1;
+  h.maxbodies = 1 << 30;
+  double tsum[3] = {0, 0, 0};
+  cudaError_t e = cudaMemsetAsync(c->plan.v.x, 0, (size_t)c->n * sizeof(double), c->cs);
+  if (e == cudaSuccess) {
+    k_fill<<<c->plan.sms * 4, 256, 0, c->cs>>>(const_cast<double*>(c->plan.v.b), c->n, 1.0);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->S, &h, sizeof h, cudaMemcpyHostToDevice, c->cs);
+  if (e != cudaSuccess) rc = cuda_err(c, e, "time_sweeps setup");
+  if (rc == PRCG_OK) rc = launch_init(c, variant, c->cs);
+  for (int it = 0; rc == PRCG_OK && it < reps; ++it) {
+    const int qr = it & 1, qw = (it + 1) & 1;
+    for (int q = 0; q < np && rc == PRCG_OK; ++q) {
+      e = cudaEventRecord(ev[q], c->cs);
+      if (e == cudaSuccess) e = c->launch(c->plan, phases[q], variant, qr, qw, c->cs);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[q + 1], c->cs);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[q + 1]);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev[q], ev[q + 1]);
+      if (e != cudaSuccess) rc = cuda_err(c, e, "time_sweeps launch");
+      tsum[q] += ms;
+    }
+  }
+  for (int q = 0; q <= np; ++q) cudaEventDestroy(ev[q]);
+  if (rc != PRCG_OK) return rc;
+  for (int q = 0; q < np; ++q) ms_per_sweep[q] = (float)(tsum[q] / reps);
+  *nsweeps = np;
+  return PRCG_OK;
+}
+
 int prcg_last_timing(const prcg_ctx* c, float* init_ms, float* loop_ms, int* iters) {
   if (!c) return PRCG_ERR_INVALID;
   if (init_ms) *init_ms = c->t_init;
@@ -611,6 +773,8 @@ int prcg_destroy(prcg_ctx* c) {
   if (c->pool) cudaFree(c->pool);
   if (c->ipool) cudaFree(c->ipool);
   if (c->vpool) cudaFree(c->vpool);
+  if (c->sell_i) cudaFree(c->sell_i);
+  if (c->sell_v) cudaFree(c->sell_v);
   if (c->partials) cudaFree(c->partials);
   if (c->S) cudaFree(c->S);
   if (c->hS) cudaFreeHost(c->hS);

@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace prcg {
 
 constexpr int kBlock = 256;             // threads per CTA for every sweep
@@ -36,6 +38,7 @@ struct DevState {
   int zero_rhs;          // b == 0: the result is x = 0
   unsigned arrive;       // CTAs that finished the current sweep
   unsigned bodies;       // executions of the while-loop body
+  int profile;           // timing runs: never finish, keep every sweep doing its work
 };
 
 // Pointers of one context; kernels take what they need by value.
@@ -127,6 +130,7 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // (and finishes the run) when ||r_k|| / ||b|| <= tol or k == maxit.
 __device__ __forceinline__ bool record_and_test(DevState* S, int k, double rho) {
   S->k = k;
+  if (S->profile) return false;
   const double rel = sqrt(rho) / sqrt(S->bnorm2);
   if (S->hist) S->hist[k] = rel;
   if (rel <= S->tol) {
@@ -143,6 +147,7 @@ __device__ __forceinline__ bool record_and_test(DevState* S, int k, double rho) 
 }
 
 __device__ __forceinline__ void breakdown(DevState* S) {
+  if (S->profile) return;
   S->status = 2;
   S->done = 1;
 }

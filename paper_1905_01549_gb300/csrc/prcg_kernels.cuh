@@ -1,12 +1,21 @@
-// Fused sweeps of HS-CG (Algorithm 1), PR-CG / M-CG (Algorithm 2 and its
+// Sweeps of HS-CG (Algorithm 1), PR-CG / M-CG (Algorithm 2 and its
 // Appendix E variant) and pipe-PR-CG / pipe-PR-M-CG (Algorithm 3).
 //
-// One sweep = one pass over the rows that does every vector update the
-// variant allows before its next global reduction, the matrix-vector
-// product(s), the partial inner products, and the grid reduction; the last
-// CTA forms the next scalars (Section 2.2.1) on the device.  Vectors that
-// other rows gather in the same sweep are double-buffered: the sweep of
-// iteration k reads buffer (k-1)&1 and writes buffer k&1.
+// On GB300 an FP64 operation costs more than the bytes it touches (the SMs
+// issue 2 FP64 FMAs per clock each), so every sweep performs each
+// arithmetic operation of the algorithm exactly once: a vector that a
+// matrix-vector product gathers is stored by the sweep that forms it and
+// read back by the next one, never recomputed at every column that uses it.
+// The dependency structure of each variant then fixes the number of sweeps
+// per iteration:
+//   HS-CG    3 sweeps, 2 reductions: x,r | p | s = A p
+//   PR-CG    2 sweeps, 1 reduction:  x,r,r~,p | s = A p + all inner products
+//   pipe-PR  1 sweep,  1 reduction:  u = A s~, w = A r~ of iteration k-1
+//            fused with the vector updates and inner products of iteration
+//            k (the recurrences of Section 2.2 make the products of k-1 the
+//            only thing iteration k's updates need from other rows).
+// Each sweep ends, where the variant has a reduction there, with the grid
+// reduction of grid_sum; its last CTA forms the next scalars on the device.
 #pragma once
 
 #include "prcg_ops.cuh"
@@ -56,22 +65,21 @@ __global__ void __launch_bounds__(kBlock) k_init_a(Op op, Pc pc, Vecs V, DevStat
   }
 }
 
-// s_0 = A p_0, s~_0 = M^{-1} s_0 (and w_0 = A r~_0, which is the same
-// product because p_0 = r~_0); mu_0, sigma_0, gamma_0; then alpha_0 (and
-// nu'_1, beta_1 for the predict-and-recompute variants).
+// s_0 = A p_0, s~_0 = M^{-1} s_0 (stored for the pipelined variants, whose
+// s~ is a recurrence); mu_0, sigma_0, gamma_0; then alpha_0 (and nu'_1,
+// beta_1 for the predict-and-recompute variants).
 template <class Op, class Pc>
 __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevState* S,
                                                    double* partials, int variant) {
   if (__ldcg(&S->done)) return;
-  const bool pipe = variant == V_PIPE || variant == V_PIPE_M || variant == V_GV;
+  const bool pipe = variant == V_PIPE || variant == V_PIPE_M;
   double acc[3] = {0.0, 0.0, 0.0};
   const double* __restrict__ p = V.p[0];
   PRCG_ROWS(i, op.n) {
     const double s = op.row(i, [&](int j) { return __ldg(p + j); });
     const double st = Pc::on ? pc(i) * s : s;
     V.s[0][i] = s;
-    if (Pc::on) V.st[0][i] = st;
-    if (pipe) V.w[0][i] = s;
+    if (Pc::on && pipe) V.st[0][i] = st;
     const double pi = __ldg(p + i);
     const double rt = Pc::on ? __ldg(V.rt[0] + i) : __ldg(V.r[0] + i);
     acc[0] += pi * s;
@@ -96,39 +104,35 @@ __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevStat
   }
 }
 
-// u_0 = A s~_0 (pipelined variants).
-template <class Op, class Pc>
-__global__ void __launch_bounds__(kBlock) k_init_c(Op op, Pc pc, Vecs V, DevState* S) {
-  if (__ldcg(&S->done)) return;
-  const double* __restrict__ st = Pc::on ? V.st[0] : V.s[0];
-  PRCG_ROWS(i, op.n) { V.u[0][i] = op.row(i, [&](int j) { return __ldg(st + j); }); }
-}
-
 // ---------------------------------------------------------------- HS-CG
-// Sweep A of iteration k: x_k, r_k, nu_k = <M^{-1} r_k, r_k>; then beta_k.
+// Sweep A of iteration k: x_k, r_k, nu_k = <M^{-1} r_k, r_k>, <r_k, r_k>;
+// then the stopping test and beta_k = nu_k / nu_{k-1}.
 template <class Op, class Pc>
 __global__ void __launch_bounds__(kBlock) k_hs_a(Op op, Pc pc, Vecs V, DevState* S,
-                                                 double* partials, int qr) {
+                                                 double* partials) {
   if (__ldcg(&S->done)) return;
   const double alpha = __ldcg(&S->alpha);
   double acc[2] = {0.0, 0.0};
-  const double* __restrict__ p = V.p[qr];
+  const double* __restrict__ p = V.p[0];
   double* __restrict__ r = V.r[0];
   const double* __restrict__ s = V.s[0];
   double* __restrict__ x = V.x;
   PRCG_ROWS(i, op.n) {
     x[i] = fma(alpha, __ldg(p + i), x[i]);
-    const double rn = fma(-alpha, s[i], r[i]);
+    const double rn = fma(-alpha, __ldg(s + i), r[i]);
     r[i] = rn;
-    const double rt = Pc::on ? pc(i) * rn : rn;
-    acc[0] += rt * rn;
-    acc[1] += rn * rn;
+    acc[1] = fma(rn, rn, acc[1]);
+    if (Pc::on && !std::is_same<Pc, PcScalar>::value) acc[0] = fma(pc(i) * rn, rn, acc[0]);
   }
   double tot[2];
   if (grid_sum<2>(acc, partials, S, tot) && threadIdx.x == 0) {
     const int k = S->k + 1;
-    const double nu = tot[0];
-    if (!record_and_test(S, k, Pc::on ? tot[1] : tot[0])) {
+    // nu_k: <r, r> unpreconditioned; d <r, r> for a constant Jacobi d
+    double nu = tot[0];
+    if (!Pc::on) nu = tot[1];
+    if (std::is_same<Pc, PcScalar>::value) nu = pc(0) * tot[1];
+    S->rho = tot[1];
+    if (!record_and_test(S, k, tot[1])) {
       if (!finite(nu) || !(nu > 0.0)) {
         breakdown(S);
       } else {
@@ -136,156 +140,184 @@ __global__ void __launch_bounds__(kBlock) k_hs_a(Op op, Pc pc, Vecs V, DevState*
         S->nu = nu;
       }
     }
-    S->rho = tot[1];
   }
 }
 
-// Sweep B of iteration k: p_k = M^{-1} r_k + beta_k p_{k-1}, s_k = A p_k,
-// mu_k = <p_k, s_k>; then alpha_k.
+// Sweep B of iteration k: p_k = M^{-1} r_k + beta_k p_{k-1} (row-local).
 template <class Op, class Pc>
-__global__ void __launch_bounds__(kBlock) k_hs_b(Op op, Pc pc, Vecs V, DevState* S,
-                                                 double* partials, int qr, int qw) {
+__global__ void __launch_bounds__(kBlock) k_hs_b(Op op, Pc pc, Vecs V, DevState* S) {
   if (__ldcg(&S->done)) return;
   const double beta = __ldcg(&S->beta);
-  double acc[1] = {0.0};
-  const double* __restrict__ p = V.p[qr];
+  double* __restrict__ p = V.p[0];
   const double* __restrict__ r = V.r[0];
-  auto pnew = [&](int j) {
-    const double rj = __ldg(r + j);
-    const double rt = Pc::on ? pc(j) * rj : rj;
-    return fma(beta, __ldg(p + j), rt);
-  };
   PRCG_ROWS(i, op.n) {
-    const double pn = pnew(i);
-    const double sn = op.row(i, pnew);
-    V.p[qw][i] = pn;
+    const double ri = __ldg(r + i);
+    const double rt = Pc::on ? pc(i) * ri : ri;
+    p[i] = fma(beta, p[i], rt);
+  }
+}
+
+// Sweep C of iteration k: s_k = A p_k, mu_k = <p_k, s_k>; then alpha_k.
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_hs_c(Op op, Pc pc, Vecs V, DevState* S,
+                                                 double* partials) {
+  if (__ldcg(&S->done)) return;
+  double acc[1] = {0.0};
+  const double* __restrict__ p = V.p[0];
+  PRCG_ROWS(i, op.n) {
+    const double sn = op.row(i, [&](int j) { return __ldg(p + j); });
     V.s[0][i] = sn;
-    acc[0] += pn * sn;
+    acc[0] = fma(__ldg(p + i), sn, acc[0]);
   }
   double tot[1];
   if (grid_sum<1>(acc, partials, S, tot) && threadIdx.x == 0) {
-    const double nu = S->nu, mu = tot[0];
+    const double mu = tot[0];
     S->mu = mu;
     if (!finite(mu) || !(mu > 0.0)) {
       breakdown(S);
     } else {
-      S->alpha = nu / mu;
+      S->alpha = S->nu / mu;
     }
   }
 }
 
 // ---------------------------------------------------------------- PR-CG / M-CG
-// One sweep per iteration k (Algorithm 2): x_k, r_k, r~_k, p_k, s_k = A p_k,
-// s~_k = M^{-1} s_k and the four inner products mu, sigma, gamma, nu (and
-// <r_k, r_k> when preconditioned), then alpha_k, nu'_{k+1}, beta_{k+1}.
+// Sweep A of iteration k (Algorithm 2, the scalars formed up front):
+// x_k, r_k, r~_k = r~_{k-1} - alpha s~_{k-1} (s~ = M^{-1} s, formed here),
+// p_k = r~_k + beta_k p_{k-1}; partial sums of nu_k = <r~_k, r_k> and
+// <r_k, r_k> go to partials_a and are added by sweep B's reduction.
 template <class Op, class Pc>
-__global__ void __launch_bounds__(kBlock) k_pr(Op op, Pc pc, Vecs V, DevState* S,
-                                               double* partials, int qr, int qw, int meurant) {
+__global__ void __launch_bounds__(kBlock) k_pr_a(Op op, Pc pc, Vecs V, DevState* S,
+                                                 double* partials_a) {
   if (__ldcg(&S->done)) return;
   const double alpha = __ldcg(&S->alpha);
   const double beta = __ldcg(&S->beta);
-  const double* __restrict__ p = V.p[qr];
-  const double* __restrict__ r = V.r[qr];
-  const double* __restrict__ rt = Pc::on ? V.rt[qr] : V.r[qr];
-  const double* __restrict__ s = V.s[qr];
   double* __restrict__ x = V.x;
-  // p_k at column j from the previous iteration's vectors
-  auto pnew = [&](int j) {
-    const double sj = __ldg(s + j);
-    const double rtn = Pc::on ? fma(-alpha, pc(j) * sj, __ldg(rt + j)) : fma(-alpha, sj, __ldg(r + j));
-    return fma(beta, __ldg(p + j), rtn);
-  };
-  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  double* __restrict__ r = V.r[0];
+  double* __restrict__ rt = V.rt[0];
+  double* __restrict__ p = V.p[0];
+  const double* __restrict__ s = V.s[0];
+  double acc[2] = {0.0, 0.0};
   PRCG_ROWS(i, op.n) {
-    const double pi = __ldg(p + i);
     const double si = __ldg(s + i);
-    x[i] = fma(alpha, pi, x[i]);
-    const double rn = fma(-alpha, si, __ldg(r + i));
-    const double rtn = Pc::on ? fma(-alpha, pc(i) * si, __ldg(rt + i)) : rn;
-    const double pn = fma(beta, pi, rtn);
-    const double sn = op.row(i, pnew);
-    const double stn = Pc::on ? pc(i) * sn : sn;
-    V.r[qw][i] = rn;
-    if (Pc::on) V.rt[qw][i] = rtn;
-    V.p[qw][i] = pn;
-    V.s[qw][i] = sn;
-    acc[0] += pn * sn;    // mu_k
-    acc[1] += rtn * sn;   // sigma_k
-    acc[2] += stn * sn;   // gamma_k
-    acc[3] += rtn * rn;   // nu_k
-    acc[4] += rn * rn;    // <r_k, r_k>
+    x[i] = fma(alpha, p[i], x[i]);
+    const double rn = fma(-alpha, si, r[i]);
+    r[i] = rn;
+    double rtn = rn;
+    if (Pc::on) {
+      rtn = fma(-alpha, pc(i) * si, rt[i]);
+      rt[i] = rtn;
+      acc[0] = fma(rtn, rn, acc[0]);
+    }
+    p[i] = fma(beta, p[i], rtn);
+    acc[1] = fma(rn, rn, acc[1]);
   }
-  double tot[5];
-  if (grid_sum<5>(acc, partials, S, tot) && threadIdx.x == 0) {
+  __shared__ double sm[2 * 32];
+  block_sum<2>(acc, sm);
+  if (threadIdx.x == 0) {
+    partials_a[blockIdx.x * 2 + 0] = acc[0];
+    partials_a[blockIdx.x * 2 + 1] = acc[1];
+  }
+}
+
+// Sweep B of iteration k: s_k = A p_k and mu_k, sigma_k = <r~_k, s_k>,
+// gamma_k = <M^{-1} s_k, s_k>; the reduction adds sweep A's nu_k and
+// <r_k, r_k>, tests for convergence and forms alpha_k, nu'_{k+1} (Eq. 2.3
+// or Meurant's form), beta_{k+1}.
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_pr_b(Op op, Pc pc, Vecs V, DevState* S,
+                                                 double* partials, const double* partials_a,
+                                                 int grid_a, int meurant) {
+  if (__ldcg(&S->done)) return;
+  const double* __restrict__ p = V.p[0];
+  const double* __restrict__ rt = Pc::on ? V.rt[0] : V.r[0];
+  double acc[3] = {0.0, 0.0, 0.0};
+  PRCG_ROWS(i, op.n) {
+    const double sn = op.row(i, [&](int j) { return __ldg(p + j); });
+    V.s[0][i] = sn;
+    acc[0] = fma(__ldg(p + i), sn, acc[0]);
+    acc[1] = fma(__ldg(rt + i), sn, acc[1]);
+    if (std::is_same<Pc, PcVec>::value)
+      acc[2] = fma(pc(i) * sn, sn, acc[2]);
+    else
+      acc[2] = fma(sn, sn, acc[2]);
+  }
+  double tot[3];
+  if (!grid_sum<3>(acc, partials, S, tot)) return;
+  // last CTA: add sweep A's partial sums (fixed order)
+  double a2[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < grid_a; b += blockDim.x) {
+    a2[0] += __ldcg(&partials_a[b * 2 + 0]);
+    a2[1] += __ldcg(&partials_a[b * 2 + 1]);
+  }
+  __shared__ double sm2[2 * 32];
+  block_sum<2>(a2, sm2);
+  if (threadIdx.x == 0) {
+    double nu = a2[0], rho = a2[1];
+    if (!Pc::on) nu = rho;
     const int k = S->k + 1;
     S->mu = tot[0];
     S->sigma = tot[1];
-    S->gamma = tot[2];
-    S->nu = tot[3];
-    S->rho = tot[4];
-    if (!record_and_test(S, k, Pc::on ? tot[4] : tot[3])) scalar_step_pr(S, meurant != 0);
+    S->gamma = std::is_same<Pc, PcScalar>::value ? pc(0) * tot[2] : tot[2];
+    S->nu = nu;
+    S->rho = rho;
+    if (!record_and_test(S, k, rho)) scalar_step_pr(S, meurant != 0);
   }
 }
 
 // ---------------------------------------------------------- pipe-PR-CG / pipe-M
-// One sweep per iteration k (Algorithm 3 with the scalars first, Section
-// 2.2.1): x_k, r_k, r~_k, w'_k, w~'_k, p_k, s_k, s~_k, then u_k = A s~_k and
-// the recomputed w_k = A r~_k in one pass over A, the inner products, and
-// alpha_k, nu'_{k+1}, beta_{k+1}.  w~ and u~ are M^{-1} w and M^{-1} u and
-// are formed where they are used instead of being stored.
+// One sweep per iteration k >= 1.  For row i it first forms
+//   u_{k-1} = A s~_{k-1},  w_{k-1} = A r~_{k-1}      (the recomputed w)
+// from the stored s~_{k-1}, r~_{k-1} (buffer qr), then Algorithm 3's updates
+//   x_k, r_k, r~_k, w'_k = w_{k-1} - alpha u_{k-1},
+//   w~'_k = M^{-1} w_{k-1} - alpha M^{-1} u_{k-1}, p_k, s_k = w'_k + beta s_{k-1},
+//   s~_k = w~'_k + beta s~_{k-1}
+// (r~_k, s~_k to buffer qw) and the inner products mu, sigma, gamma, nu of
+// iteration k; u and w never leave registers.
 template <class Op, class Pc>
 __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState* S,
                                                  double* partials, int qr, int qw, int meurant) {
   if (__ldcg(&S->done)) return;
   const double alpha = __ldcg(&S->alpha);
   const double beta = __ldcg(&S->beta);
-  const double* __restrict__ p = V.p[qr];
-  const double* __restrict__ r = V.r[qr];
-  const double* __restrict__ rt = Pc::on ? V.rt[qr] : V.r[qr];
-  const double* __restrict__ s = V.s[qr];
-  const double* __restrict__ st = Pc::on ? V.st[qr] : V.s[qr];
-  const double* __restrict__ w = V.w[qr];
-  const double* __restrict__ u = V.u[qr];
+  const double* __restrict__ rt_o = Pc::on ? V.rt[qr] : V.r[qr];
+  const double* __restrict__ st_o = Pc::on ? V.st[qr] : V.s[qr];
+  const double* __restrict__ r_o = V.r[qr];
+  const double* __restrict__ s_o = V.s[qr];
   double* __restrict__ x = V.x;
-  // r~_k at column j
-  auto rtnew = [&](int j) { return fma(-alpha, __ldg(st + j), __ldg(rt + j)); };
-  // s~_k = w~'_k + beta_k s~_{k-1} at column j
-  auto stnew = [&](int j) {
-    if (Pc::on) {
-      const double dj = pc(j);
-      return fma(beta, __ldg(st + j), fma(-alpha, dj * __ldg(u + j), dj * __ldg(w + j)));
-    }
-    return fma(beta, __ldg(st + j), fma(-alpha, __ldg(u + j), __ldg(w + j)));
-  };
+  double* __restrict__ p = V.p[0];
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   PRCG_ROWS(i, op.n) {
-    const double pi = __ldg(p + i);
-    const double si = __ldg(s + i);
-    const double wi = __ldg(w + i);
-    const double ui = __ldg(u + i);
-    x[i] = fma(alpha, pi, x[i]);
-    const double rn = fma(-alpha, si, __ldg(r + i));
-    const double rtn = Pc::on ? rtnew(i) : rn;
-    const double wp = fma(-alpha, ui, wi);
-    const double pn = fma(beta, pi, rtn);
-    const double sn = fma(beta, si, wp);
-    const double stn = Pc::on ? stnew(i) : sn;
-    double un, wn;
-    op.row2(i, stnew, rtnew, un, wn);
-    V.r[qw][i] = rn;
+    double u, w;
+    op.row2(i, [&](int j) { return __ldg(st_o + j); }, [&](int j) { return __ldg(rt_o + j); },
+            u, w);
+    const double si = __ldg(s_o + i);
+    x[i] = fma(alpha, p[i], x[i]);
+    const double rn = fma(-alpha, si, __ldg(r_o + i));
+    const double wp = fma(-alpha, u, w);
+    double rtn = rn, sn, stn;
     if (Pc::on) {
+      const double di = pc(i);
+      const double sti = __ldg(st_o + i);
+      rtn = fma(-alpha, sti, __ldg(rt_o + i));
+      const double wtp = fma(-alpha, di * u, di * w);
+      sn = fma(beta, si, wp);
+      stn = fma(beta, sti, wtp);
       V.rt[qw][i] = rtn;
       V.st[qw][i] = stn;
+    } else {
+      sn = fma(beta, si, wp);
+      stn = sn;
     }
-    V.p[qw][i] = pn;
+    const double pn = fma(beta, p[i], rtn);
+    p[i] = pn;
+    V.r[qw][i] = rn;
     V.s[qw][i] = sn;
-    V.w[qw][i] = wn;
-    V.u[qw][i] = un;
-    acc[0] += pn * sn;
-    acc[1] += rtn * sn;
-    acc[2] += stn * sn;
-    acc[3] += rtn * rn;
-    acc[4] += rn * rn;
+    acc[0] = fma(pn, sn, acc[0]);
+    acc[1] = fma(rtn, sn, acc[1]);
+    acc[2] = fma(stn, sn, acc[2]);
+    acc[3] = fma(rtn, rn, acc[3]);
+    acc[4] = fma(rn, rn, acc[4]);
   }
   double tot[5];
   if (grid_sum<5>(acc, partials, S, tot) && threadIdx.x == 0) {
@@ -295,7 +327,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
     S->gamma = tot[2];
     S->nu = tot[3];
     S->rho = tot[4];
-    if (!record_and_test(S, k, Pc::on ? tot[4] : tot[3])) scalar_step_pr(S, meurant != 0);
+    if (!record_and_test(S, k, tot[4])) scalar_step_pr(S, meurant != 0);
   }
 }
 

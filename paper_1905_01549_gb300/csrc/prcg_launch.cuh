@@ -10,12 +10,13 @@ namespace prcg {
 enum Phase {
   PH_INIT_A = 0,
   PH_INIT_B = 1,
-  PH_INIT_C = 2,
-  PH_HS_A = 3,
-  PH_HS_B = 4,
-  PH_PR = 5,
-  PH_PIPE = 6,
-  PH_TRUE_RES = 7
+  PH_HS_A = 2,
+  PH_HS_B = 3,
+  PH_HS_C = 4,
+  PH_PR_A = 5,
+  PH_PR_B = 6,
+  PH_PIPE = 7,
+  PH_TRUE_RES = 8
 };
 
 struct Plan {
@@ -24,6 +25,7 @@ struct Plan {
   Vecs v;
   DevState* S;
   double* partials;
+  double* partials_a;    // PR sweep A's per-CTA sums
   int sms;
 };
 
@@ -63,24 +65,31 @@ cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, 
       k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, variant);
       break;
     }
-    case PH_INIT_C: {
-      auto k = k_init_c<Op, Pc>;
-      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S);
-      break;
-    }
     case PH_HS_A: {
       auto k = k_hs_a<Op, Pc>;
-      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr);
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);
       break;
     }
     case PH_HS_B: {
       auto k = k_hs_b<Op, Pc>;
-      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw);
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S);
       break;
     }
-    case PH_PR: {
-      auto k = k_pr<Op, Pc>;
-      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw, meurant);
+    case PH_HS_C: {
+      auto k = k_hs_c<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);
+      break;
+    }
+    case PH_PR_A: {
+      auto k = k_pr_a<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials_a);
+      break;
+    }
+    case PH_PR_B: {
+      auto k = k_pr_b<Op, Pc>;
+      const int grid_a = grid_for(k_pr_a<Op, Pc>, n, P.sms);
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, P.partials_a,
+                                                   grid_a, meurant);
       break;
     }
     case PH_PIPE: {

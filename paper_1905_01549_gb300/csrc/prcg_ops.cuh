@@ -12,7 +12,7 @@
 
 namespace prcg {
 
-enum OpKind { OP_CSR = 0, OP_ST2 = 1, OP_ST3 = 2, OP_VC2 = 3, OP_VC3 = 4 };
+enum OpKind { OP_CSR = 0, OP_ST2 = 1, OP_ST3 = 2, OP_VC2 = 3, OP_VC3 = 4, OP_SELL = 5 };
 enum PcKind { PC_NONE = 0, PC_SCALAR = 1, PC_VEC = 2 };
 
 // Host-side description of an operator; the device structs below are built
@@ -29,6 +29,10 @@ struct OpDesc {
   const double* fz;
   const double* adiag;   // variable-coefficient diagonal incl. shift
   double cdiag;          // constant-coefficient diagonal 2*dim + shift
+  const int* sptr;       // SELL-32: first entry of each 32-row slice
+  const int* slen;       // SELL-32: entries per row in each slice
+  const int* scol;       // SELL-32 column indices, slice-major, row-minor
+  const double* sval;    // SELL-32 values (padding: column = row, value 0)
 };
 
 struct PcDesc {
@@ -66,6 +70,57 @@ struct CsrOp {
   }
 };
 
+// ---------------------------------------------------------------- SELL-32
+// The CSR matrix re-laid out in slices of 32 consecutive rows; entry t of
+// row 32 s + l sits at sptr[s] + 32 t + l, so the 32 lanes of a warp (which
+// own 32 consecutive rows) read each entry position with one coalesced
+// access and run the same trip count.  Built from the caller's CSR at
+// context creation; sums run in the same column order as the CSR rows.
+struct SellOp {
+  const int* __restrict__ sptr;
+  const int* __restrict__ slen;
+  const int* __restrict__ scol;
+  const double* __restrict__ sval;
+  int n;
+  explicit SellOp(const OpDesc& o) : sptr(o.sptr), slen(o.slen), scol(o.scol), sval(o.sval), n(o.n) {}
+  // Entries t < 8 are loaded with predication (all loads of a row are in
+  // flight together); longer rows continue in a plain loop.
+  template <class F>
+  __device__ __forceinline__ void visit(int i, F&& f) const {
+    const int sl = i >> 5;
+    const int base = __ldg(sptr + sl) + (i & 31);
+    const int L = __ldg(slen + sl);
+    int j[8];
+    double a[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const bool ok = t < L;
+      j[t] = ok ? __ldg(scol + base + 32 * t) : i;
+      a[t] = ok ? __ldg(sval + base + 32 * t) : 0.0;
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (t < L) f(j[t], a[t]);
+    for (int t = 8; t < L; ++t) f(__ldg(scol + base + 32 * t), __ldg(sval + base + 32 * t));
+  }
+  template <class G>
+  __device__ __forceinline__ double row(int i, G&& g) const {
+    double acc = 0.0;
+    visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
+    return acc;
+  }
+  template <class G1, class G2>
+  __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
+    double c1 = 0.0, c2 = 0.0;
+    visit(i, [&](int j, double a) {
+      c1 = fma(a, g1(j), c1);
+      c2 = fma(a, g2(j), c2);
+    });
+    a1 = c1;
+    a2 = c2;
+  }
+};
+
 // ------------------------------------------- constant-coefficient stencil
 // 5-point (DIM 2) / 7-point (DIM 3) Poisson with Dirichlet-0 boundary:
 // y_i = cdiag * g(i) - sum over existing neighbours g(j).
@@ -74,21 +129,23 @@ struct StencilOp {
   int nx, ny, nz, n;
   double cdiag;
   explicit StencilOp(const OpDesc& o) : nx(o.nx), ny(o.ny), nz(o.nz), n(o.n), cdiag(o.cdiag) {}
+  // f(j, coefficient) for the 2*DIM+1 entries in increasing column order.
+  // Missing neighbours (Dirichlet boundary) are visited as column i with
+  // coefficient 0, so every load is issued unconditionally.
   template <class F>
   __device__ __forceinline__ void visit(int i, F&& f) const {
-    // f(j, coefficient) in increasing column order
     const int x = i % nx;
     const int yz = i / nx;
     const int y = yz % ny;
     const int z = yz / ny;
     const int pl = nx * ny;
-    if (DIM == 3 && z > 0) f(i - pl, -1.0);
-    if (y > 0) f(i - nx, -1.0);
-    if (x > 0) f(i - 1, -1.0);
+    if (DIM == 3) f(z > 0 ? i - pl : i, z > 0 ? -1.0 : 0.0);
+    f(y > 0 ? i - nx : i, y > 0 ? -1.0 : 0.0);
+    f(x > 0 ? i - 1 : i, x > 0 ? -1.0 : 0.0);
     f(i, cdiag);
-    if (x < nx - 1) f(i + 1, -1.0);
-    if (y < ny - 1) f(i + nx, -1.0);
-    if (DIM == 3 && z < nz - 1) f(i + pl, -1.0);
+    f(x < nx - 1 ? i + 1 : i, x < nx - 1 ? -1.0 : 0.0);
+    f(y < ny - 1 ? i + nx : i, y < ny - 1 ? -1.0 : 0.0);
+    if (DIM == 3) f(z < nz - 1 ? i + pl : i, z < nz - 1 ? -1.0 : 0.0);
   }
   template <class G>
   __device__ __forceinline__ double row(int i, G&& g) const {
@@ -126,13 +183,20 @@ struct VarStencilOp {
     const int y = yz % ny;
     const int z = yz / ny;
     const int pl = nx * ny;
-    if (DIM == 3 && z > 0) f(i - pl, -__ldg(fz + i));
-    if (y > 0) f(i - nx, -__ldg(fy + (z * (ny + 1) + y) * nx + x));
-    if (x > 0) f(i - 1, -__ldg(fx + yz * (nx + 1) + x));
+    // face coefficients of the cell (boundary faces are valid addresses)
+    const double czm = DIM == 3 ? __ldg(fz + i) : 0.0;
+    const double cym = __ldg(fy + (z * (ny + 1) + y) * nx + x);
+    const double cxm = __ldg(fx + yz * (nx + 1) + x);
+    const double cxp = __ldg(fx + yz * (nx + 1) + x + 1);
+    const double cyp = __ldg(fy + (z * (ny + 1) + y + 1) * nx + x);
+    const double czp = DIM == 3 ? __ldg(fz + i + pl) : 0.0;
+    if (DIM == 3) f(z > 0 ? i - pl : i, z > 0 ? -czm : 0.0);
+    f(y > 0 ? i - nx : i, y > 0 ? -cym : 0.0);
+    f(x > 0 ? i - 1 : i, x > 0 ? -cxm : 0.0);
     f(i, __ldg(adiag + i));
-    if (x < nx - 1) f(i + 1, -__ldg(fx + yz * (nx + 1) + x + 1));
-    if (y < ny - 1) f(i + nx, -__ldg(fy + (z * (ny + 1) + y + 1) * nx + x));
-    if (DIM == 3 && z < nz - 1) f(i + pl, -__ldg(fz + i + pl));
+    f(x < nx - 1 ? i + 1 : i, x < nx - 1 ? -cxp : 0.0);
+    f(y < ny - 1 ? i + nx : i, y < ny - 1 ? -cyp : 0.0);
+    if (DIM == 3) f(z < nz - 1 ? i + pl : i, z < nz - 1 ? -czp : 0.0);
   }
   template <class G>
   __device__ __forceinline__ double row(int i, G&& g) const {
