@@ -169,6 +169,48 @@ const char* prcg_last_error(const prcg_ctx* ctx);
 /* prcg_n -- the number of unknowns of the context (or -1 for NULL). */
 int64_t prcg_n(const prcg_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Batched solver: many independent SPD systems of uneven size in one launch.
+ *
+ * Each system i is the 2D 5-point operator of prcg_create_stencil (face_coeff
+ * NULL) on an nx[i] x ny[i] grid with diagonal shift shift[i] >= 0.  One
+ * persistent kernel (captured in a CUDA graph with the reset of its work
+ * queue) solves all of them with PR-CG (Algorithm 2): each thread-block
+ * cluster takes the next system from a device queue ordered by estimated
+ * cost (n * sqrt(condition number), largest first) and iterates it to
+ * ||r_k|| / ||b|| <= tol with cluster-wide reductions in distributed shared
+ * memory.  Cluster and CTA sizes come from prcg_batched_configure (the
+ * Python autotuner picks them); the default is 1 CTA of 256 threads.
+ * ------------------------------------------------------------------------ */
+typedef struct prcg_batch prcg_batch;
+
+/* nx, ny, shift: host arrays of nsys entries (copied).  precond as above
+ * (Jacobi is the scalar 1 / (4 + shift[i])).  n_i = nx[i]*ny[i] < 2^30. */
+int prcg_batched_create(prcg_batch** out, int nsys, const int32_t* nx, const int32_t* ny,
+                        const double* shift, int precond, void* cuda_stream);
+
+/* cluster in {1, 2, 4, 8, 16} CTAs, threads per CTA a multiple of 32 in
+ * [64, 1024]; PRCG_ERR_UNSUPPORTED if the cluster cannot be resident. */
+int prcg_batched_configure(prcg_batch* bt, int cluster, int threads);
+
+/* b, x: sum(n_i) doubles each, systems concatenated in creation order (host or
+ * device); x holds x_0 on entry and x_K per system on return.  iters_out,
+ * status_out (int32[nsys]) and true_relres_out (double[nsys], ||b - A x|| /
+ * ||b|| per system) may be NULL.  Returns the worst per-system status
+ * (PRCG_OK < PRCG_NOT_CONVERGED < PRCG_BREAKDOWN) or a negative error. */
+int prcg_batched_solve(prcg_batch* bt, const double* b, double* x, double tol, int maxit,
+                       int32_t* iters_out, int32_t* status_out, double* true_relres_out);
+
+/* device time (CUDA events) of the last batched solve's graph launch */
+int prcg_batched_last_ms(const prcg_batch* bt, float* ms);
+
+/* the launch configuration in use: cluster size, CTA size, resident clusters */
+int prcg_batched_config(const prcg_batch* bt, int* cluster, int* threads, int* clusters);
+
+const char* prcg_batched_last_error(const prcg_batch* bt);
+
+int prcg_batched_destroy(prcg_batch* bt);
+
 /*
  * prcg_pr_solve_stencil_noalloc -- PR-CG on a small constant-coefficient
  * stencil system without any device allocation.  The paper has no

@@ -103,3 +103,53 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BatchedSolver:
+    """Many shifted 2D 5-point systems of uneven size solved by one persistent
+    PR-CG launch (C ABI prcg_batched_*)."""
+
+    def __init__(self, nx, ny, shift, precond: str = "none", stream=None):
+        self.nx = np.asarray(nx, dtype=np.int32)
+        self.ny = np.asarray(ny, dtype=np.int32)
+        self.shift = np.asarray(shift, dtype=np.float64)
+        self.precond = PRECONDS[precond]
+        self.sizes = self.nx.astype(np.int64) * self.ny
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)])
+        self.total = int(self.offsets[-1])
+        self.handle = binding.prcg_batched_create(self.nx, self.ny, self.shift, self.precond, stream)
+
+    def configure(self, cluster: int, threads: int):
+        binding.prcg_batched_configure(self.handle, cluster, threads)
+
+    def config(self):
+        return binding.prcg_batched_config(self.handle)
+
+    def tune(self, b, x0=None, tol: float = 1e-8, maxit: int = 100000, **kw):
+        from . import autotune
+        torch = _torch()
+        if x0 is None:
+            x0 = torch.zeros(self.total, dtype=torch.float64, device="cuda")
+        key = autotune.batch_key(self.nx, self.ny, self.shift, self.precond, tol)
+        return autotune.tune(self.handle, b, x0, tol, maxit, key=key, **kw)
+
+    def solve(self, b, x0=None, tol: float = 1e-8, maxit: int = 100000, true_relres: bool = False):
+        """Returns (x, iters[nsys], status[nsys], true_relres[nsys] or None, worst status, ms)."""
+        torch = _torch()
+        x = x0 if x0 is not None else torch.zeros(self.total, dtype=torch.float64, device="cuda")
+        iters = np.zeros(len(self.nx), dtype=np.int32)
+        status = np.zeros(len(self.nx), dtype=np.int32)
+        trr = np.zeros(len(self.nx)) if true_relres else None
+        worst = binding.prcg_batched_solve(self.handle, b, x, tol, maxit, iters, status, trr)
+        return x, iters, status, trr, worst, binding.prcg_batched_last_ms(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            binding.prcg_batched_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,93 @@
+"""Autotuner for the batched persistent solver's launch configuration.
+
+The batched kernel (csrc/prcg_batched.cu) runs one PR-CG solver per
+thread-block cluster; the best cluster size (1..16 CTAs) and CTA size
+depend on the size mix of the batch: small systems want many independent
+solvers, large ones want several SMs per system so the largest solve does
+not set the makespan.  The tuner times each candidate on the batch itself
+(the device time of the solve's graph launch, CUDA events), keeps the
+fastest and caches the choice in a JSON file keyed by the batch's shape.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+from typing import Iterable, Optional, Sequence, Tuple
+
+from . import binding
+
+DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = (
+    (1, 256), (1, 512), (1, 1024), (2, 256), (2, 512), (4, 256), (4, 512), (8, 256), (8, 512),
+    (16, 256))
+
+
+def default_cache_path() -> str:
+    base = os.environ.get("PRCG_TUNE_CACHE")
+    if base:
+        return base
+    return os.path.join(os.path.expanduser("~"), ".cache", "prcg_gb300", "batched_tuning.json")
+
+
+def batch_key(nx: Sequence[int], ny: Sequence[int], shift: Sequence[float], precond: int,
+              tol: float) -> str:
+    h = hashlib.sha256()
+    for arr in (nx, ny):
+        h.update(",".join(str(int(v)) for v in arr).encode())
+    h.update(",".join(f"{float(v):.6g}" for v in shift).encode())
+    h.update(f"{precond}:{tol:.3g}".encode())
+    return h.hexdigest()[:24]
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def tune(bt, b, x0, tol: float, maxit: int, key: Optional[str] = None,
+         candidates: Iterable[Tuple[int, int]] = DEFAULT_CANDIDATES, reps: int = 1,
+         cache_path: Optional[str] = None, use_cache: bool = True):
+    """Pick (cluster, threads) for batch handle `bt`; returns (cluster, threads, ms, table).
+
+    b and x0 are the batch's concatenated right-hand side and initial guess
+    (x0 is copied for every trial and left unchanged)."""
+    import torch
+    cache_path = cache_path or default_cache_path()
+    cache = _load(cache_path) if use_cache else {}
+    if key and use_cache and key in cache:
+        ent = cache[key]
+        binding.prcg_batched_configure(bt, ent["cluster"], ent["threads"])
+        return ent["cluster"], ent["threads"], ent["ms"], ent.get("table", [])
+    table = []
+    best = None
+    x = torch.empty_like(x0)
+    for cluster, threads in candidates:
+        try:
+            binding.prcg_batched_configure(bt, cluster, threads)
+        except binding.PrcgError:
+            table.append((cluster, threads, None))
+            continue
+        times = []
+        for _ in range(reps + 1):   # first run instantiates the graph
+            x.copy_(x0)
+            binding.prcg_batched_solve(bt, b, x, tol, maxit)
+            times.append(binding.prcg_batched_last_ms(bt))
+        ms = min(times[1:]) if reps > 0 else times[0]
+        table.append((cluster, threads, ms))
+        if best is None or ms < best[2]:
+            best = (cluster, threads, ms)
+    if best is None:
+        raise RuntimeError("no batched configuration could be launched")
+    binding.prcg_batched_configure(bt, best[0], best[1])
+    if key:
+        cache = _load(cache_path)
+        cache[key] = {"cluster": best[0], "threads": best[1], "ms": best[2], "table": table}
+        os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1)
+        os.replace(tmp, cache_path)
+    return best[0], best[1], best[2], table

@@ -31,7 +31,9 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_INVALID", 
 EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_solve", "prcg_last_timing",
            "prcg_time_sweeps",
            "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n",
-           "prcg_pr_solve_stencil_noalloc")
+           "prcg_pr_solve_stencil_noalloc", "prcg_batched_create", "prcg_batched_configure",
+           "prcg_batched_solve", "prcg_batched_last_ms", "prcg_batched_config",
+           "prcg_batched_last_error", "prcg_batched_destroy")
 
 
 class PrcgError(RuntimeError):
@@ -83,6 +85,20 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                   vp, vp, ctypes.c_double, ctypes.c_int, vp,
                                                   _c_int_p, vp]
     lib.prcg_pr_solve_stencil_noalloc.restype = ctypes.c_int
+    lib.prcg_batched_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp, vp, vp, ctypes.c_int, vp]
+    lib.prcg_batched_create.restype = ctypes.c_int
+    lib.prcg_batched_configure.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    lib.prcg_batched_configure.restype = ctypes.c_int
+    lib.prcg_batched_solve.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int, vp, vp, vp]
+    lib.prcg_batched_solve.restype = ctypes.c_int
+    lib.prcg_batched_last_ms.argtypes = [vp, _c_float_p]
+    lib.prcg_batched_last_ms.restype = ctypes.c_int
+    lib.prcg_batched_config.argtypes = [vp, _c_int_p, _c_int_p, _c_int_p]
+    lib.prcg_batched_config.restype = ctypes.c_int
+    lib.prcg_batched_last_error.argtypes = [vp]
+    lib.prcg_batched_last_error.restype = ctypes.c_char_p
+    lib.prcg_batched_destroy.argtypes = [vp]
+    lib.prcg_batched_destroy.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -198,3 +214,51 @@ def prcg_pr_solve_stencil_noalloc(dim, nx, ny, nz, diag_shift, precond, b, x, to
     if rc < 0:
         raise PrcgError(rc, "prcg_pr_solve_stencil_noalloc failed")
     return rc, iters.value
+
+
+def _bcheck(code, bt):
+    if code < 0:
+        msg = load().prcg_batched_last_error(bt).decode(errors="replace") if bt else ""
+        raise PrcgError(code, msg or "batched call failed")
+    return code
+
+
+def prcg_batched_create(nx, ny, shift, precond=PRCG_PRECOND_NONE, stream=None):
+    """Create a batch of shifted 2D 5-point systems; returns the handle."""
+    nx = np.ascontiguousarray(nx, dtype=np.int32)
+    ny = np.ascontiguousarray(ny, dtype=np.int32)
+    shift = np.ascontiguousarray(shift, dtype=np.float64)
+    out = ctypes.c_void_p()
+    _bcheck(load().prcg_batched_create(ctypes.byref(out), len(nx), ptr(nx), ptr(ny), ptr(shift),
+                                       int(precond), _stream_ptr(stream)), None)
+    return out.value
+
+
+def prcg_batched_configure(bt, cluster, threads):
+    return _bcheck(load().prcg_batched_configure(bt, int(cluster), int(threads)), bt)
+
+
+def prcg_batched_solve(bt, b, x, tol, maxit, iters=None, status=None, true_relres=None):
+    """Solve every system of the batch; returns the worst status."""
+    return _bcheck(load().prcg_batched_solve(bt, ptr(b), ptr(x), float(tol), int(maxit), ptr(iters),
+                                             ptr(status), ptr(true_relres)), bt)
+
+
+def prcg_batched_last_ms(bt) -> float:
+    ms = ctypes.c_float()
+    _bcheck(load().prcg_batched_last_ms(bt, ctypes.byref(ms)), bt)
+    return ms.value
+
+
+def prcg_batched_config(bt):
+    c, t, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcheck(load().prcg_batched_config(bt, ctypes.byref(c), ctypes.byref(t), ctypes.byref(k)), bt)
+    return c.value, t.value, k.value
+
+
+def prcg_batched_last_error(bt) -> str:
+    return load().prcg_batched_last_error(bt).decode(errors="replace")
+
+
+def prcg_batched_destroy(bt):
+    return load().prcg_batched_destroy(bt)

@@ -1,0 +1,538 @@
+// Batched PR-CG: many independent 2D 5-point (shifted) stencil systems of
+// uneven size solved by one persistent kernel launch.
+//
+// Every thread-block cluster is a solver: its leader CTA takes the next
+// system from a device work queue (systems ordered by estimated cost,
+// largest first), and the cluster runs Algorithm 2 on it -- sweep A (x, r,
+// r~, p and the partial nu, <r, r>), a cluster barrier, sweep B (s = A p and
+// mu, sigma, gamma) and one cluster-wide reduction through distributed shared
+// memory -- until the system converges, then takes the next one.  The
+// reduction adds the CTA partials in rank order in every CTA, so all CTAs
+// of a cluster hold bitwise-identical scalars and take identical decisions;
+// the only synchronisation is the hardware cluster barrier (no CTA ever
+// spins on memory).  Cluster size and CTA size are launch parameters chosen
+// by the autotuner (paper_1905_01549_gb300/autotune.py).
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/prcg.h"
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+struct BatchSys {
+  long long off;  // first row in the concatenated vectors
+  int nx, ny;
+  double cdiag;   // 4 + shift
+  double d;       // Jacobi 1 / cdiag, or 1
+};
+
+constexpr int kMaxThreads = 1024;
+
+template <int NV>
+__device__ __forceinline__ void cta_sum(double (&v)[NV], double* sm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+#pragma unroll
+  for (int m = 0; m < NV; ++m)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_down_sync(0xffffffffu, v[m], o);
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int m = 0; m < NV; ++m) sm[m * 32 + wid] = v[m];
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+      double t = lane < nw ? sm[m * 32 + lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      v[m] = t;
+    }
+  }
+}
+
+// Cluster-wide sum: CTA totals go to a double-buffered shared slot, one
+// cluster barrier, then every thread adds all ranks' slots in rank order.
+template <int NV>
+__device__ __forceinline__ void cluster_sum(double (&v)[NV], double* sm, double* slots, int& parity,
+                                            cg::cluster_group& cl, double (&tot)[NV]) {
+  cta_sum<NV>(v, sm);
+  double* mine = slots + parity * 8;
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int m = 0; m < NV; ++m) mine[m] = v[m];
+  cl.sync();
+#pragma unroll
+  for (int m = 0; m < NV; ++m) tot[m] = 0.0;
+  const unsigned nb = cl.num_blocks();
+  for (unsigned r = 0; r < nb; ++r) {
+    const double* rs = cl.map_shared_rank(mine, r);
+#pragma unroll
+    for (int m = 0; m < NV; ++m) tot[m] += rs[m];
+  }
+  parity ^= 1;
+}
+
+__device__ __forceinline__ double stencil_row(const BatchSys& q, const double* __restrict__ v, int i) {
+  const int x = i % q.nx, y = i / q.nx;
+  double acc = 0.0;
+  if (y > 0) acc = fma(-1.0, __ldcg(v + i - q.nx), acc);
+  if (x > 0) acc = fma(-1.0, __ldcg(v + i - 1), acc);
+  acc = fma(q.cdiag, __ldcg(v + i), acc);
+  if (x < q.nx - 1) acc = fma(-1.0, __ldcg(v + i + 1), acc);
+  if (y < q.ny - 1) acc = fma(-1.0, __ldcg(v + i + q.nx), acc);
+  return acc;
+}
+
+struct BatchArgs {
+  const BatchSys* sys;
+  const int* order;     // systems by decreasing estimated cost
+  int nsys;
+  const double* b;
+  double* x;
+  double* r;
+  double* rt;
+  double* p;
+  double* s;
+  double tol;
+  int maxit;
+  int jacobi;
+  int* iters;
+  int* status;
+  int* queue;
+};
+
+__global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  const unsigned crank = cl.block_rank();
+  const int G = (int)(cl.num_blocks() * blockDim.x);
+  const int g0 = (int)(crank * blockDim.x + threadIdx.x);
+  __shared__ double sm[5 * 32];
+  __shared__ double slots[2 * 8];
+  __shared__ int s_next;
+  int parity = 0;
+  for (;;) {
+    if (crank == 0 && threadIdx.x == 0) s_next = atomicAdd(a.queue, 1);
+    cl.sync();
+    const int qi = *cl.map_shared_rank(&s_next, 0);
+    cl.sync();  // the leader's slot is read by all before it is rewritten
+    if (qi >= a.nsys) break;
+    const int id = a.order[qi];
+    const BatchSys q = a.sys[id];
+    const int n = q.nx * q.ny;
+    const double* b = a.b + q.off;
+    double* x = a.x + q.off;
+    double* r = a.r + q.off;
+    double* rt = a.rt + q.off;
+    double* p = a.p + q.off;
+    double* s = a.s + q.off;
+    const double d = q.d;
+    // initialize(): r_0 = b - A x_0, r~_0 = d r_0, p_0 = r~_0
+    double i3[3] = {0.0, 0.0, 0.0};
+    for (int i = g0; i < n; i += G) {
+      const double bi = b[i];
+      const double ri = bi - stencil_row(q, x, i);
+      const double rti = a.jacobi ? d * ri : ri;
+      r[i] = ri;
+      rt[i] = rti;
+      p[i] = rti;
+      i3[0] = fma(rti, ri, i3[0]);
+      i3[1] = fma(ri, ri, i3[1]);
+      i3[2] = fma(bi, bi, i3[2]);
+    }
+    double t3[3];
+    cluster_sum<3>(i3, sm, slots, parity, cl, t3);
+    double nu = t3[0];
+    const double bnorm = sqrt(t3[2]);
+    int status = -100, K = 0;
+    if (t3[2] == 0.0) {
+      status = 0;
+      for (int i = g0; i < n; i += G) x[i] = 0.0;
+    } else if (sqrt(t3[1]) / bnorm <= a.tol) {
+      status = 0;
+    } else if (a.maxit == 0) {
+      status = 1;
+    }
+    double alpha = 0.0, beta = 0.0;
+    if (status == -100) {
+      // s_0 = A p_0; mu_0, sigma_0, gamma_0
+      double j3[3] = {0.0, 0.0, 0.0};
+      for (int i = g0; i < n; i += G) {
+        const double si = stencil_row(q, p, i);
+        s[i] = si;
+        j3[0] = fma(p[i], si, j3[0]);
+        j3[1] = fma(rt[i], si, j3[1]);
+        j3[2] = fma(si, si, j3[2]);
+      }
+      double u3[3];
+      cluster_sum<3>(j3, sm, slots, parity, cl, u3);
+      double mu = u3[0], sigma = u3[1], gamma = a.jacobi ? d * u3[2] : u3[2];
+      for (int k = 1; k <= a.maxit; ++k) {
+        // scalar step (identical in every thread of the cluster)
+        alpha = nu / mu;
+        const double nu_pred = nu - 2.0 * alpha * sigma + alpha * alpha * gamma;
+        if (!isfinite(nu) || !isfinite(mu) || !(mu > 0.0) || nu < 0.0 || !isfinite(nu_pred) ||
+            nu_pred < 0.0 || nu == 0.0) {
+          status = 2;
+          K = k - 1;
+          break;
+        }
+        beta = nu_pred / nu;
+        // sweep A: x_k, r_k, r~_k, p_k
+        double a2[2] = {0.0, 0.0};
+        for (int i = g0; i < n; i += G) {
+          const double si = s[i];
+          const double pi = p[i];
+          x[i] = fma(alpha, pi, x[i]);
+          const double rn = fma(-alpha, si, r[i]);
+          r[i] = rn;
+          double rtn = rn;
+          if (a.jacobi) {
+            rtn = fma(-alpha, d * si, rt[i]);
+            rt[i] = rtn;
+          }
+          p[i] = fma(beta, pi, rtn);
+          a2[0] = fma(rtn, rn, a2[0]);
+          a2[1] = fma(rn, rn, a2[1]);
+        }
+        cl.sync();  // p_k complete in every CTA before the product
+        // sweep B: s_k = A p_k, mu_k, sigma_k, gamma_k
+        double a5[5] = {a2[0], a2[1], 0.0, 0.0, 0.0};
+        const double* rtv = a.jacobi ? rt : r;
+        for (int i = g0; i < n; i += G) {
+          const double sn = stencil_row(q, p, i);
+          s[i] = sn;
+          a5[2] = fma(p[i], sn, a5[2]);
+          a5[3] = fma(rtv[i], sn, a5[3]);
+          a5[4] = fma(sn, sn, a5[4]);
+        }
+        double t5[5];
+        cluster_sum<5>(a5, sm, slots, parity, cl, t5);
+        nu = t5[0];
+        mu = t5[2];
+        sigma = t5[3];
+        gamma = a.jacobi ? d * t5[4] : t5[4];
+        K = k;
+        if (sqrt(t5[1]) / bnorm <= a.tol) {
+          status = 0;
+          break;
+        }
+        if (k == a.maxit) status = 1;
+      }
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+      a.iters[id] = K;
+      a.status[id] = status;
+    }
+  }
+}
+
+// ||b - A x|| / ||b|| per system (one CTA per system, grid-stride over systems).
+__global__ void k_batched_true_res(BatchArgs a, double* out) {
+  __shared__ double sm[2 * 32];
+  for (int id = blockIdx.x; id < a.nsys; id += gridDim.x) {
+    const BatchSys q = a.sys[id];
+    const int n = q.nx * q.ny;
+    double v[2] = {0.0, 0.0};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const double bi = a.b[q.off + i];
+      const double t = bi - stencil_row(q, a.x + q.off, i);
+      v[0] = fma(t, t, v[0]);
+      v[1] = fma(bi, bi, v[1]);
+    }
+    cta_sum<2>(v, sm);
+    if (threadIdx.x == 0) out[id] = v[1] > 0.0 ? sqrt(v[0]) / sqrt(v[1]) : 0.0;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+struct prcg_batch {
+  int nsys = 0;
+  long long total = 0;
+  int precond = 0;
+  cudaStream_t user = nullptr, cs = nullptr;
+  cudaEvent_t ev_user = nullptr, ev0 = nullptr, ev1 = nullptr;
+  BatchSys* d_sys = nullptr;
+  int* d_order = nullptr;
+  int* d_iters = nullptr;
+  int* d_status = nullptr;
+  int* d_queue = nullptr;
+  double* d_true = nullptr;
+  double* pool = nullptr;  // b, x, r, r~, p, s
+  int cluster = 1;
+  int threads = 256;
+  int clusters = 0;
+  cudaGraphExec_t exec = nullptr;
+  double graph_tol = -1.0;   // parameters the instantiated graph was captured with
+  int graph_maxit = -1;
+  float last_ms = 0.f;
+  std::string err;
+};
+
+namespace {
+
+int berr(prcg_batch* bt, int code, const std::string& m) {
+  if (bt) bt->err = m;
+  return code;
+}
+
+#define BCK(call)                                                              \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess) return berr(bt, PRCG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+BatchArgs args_of(prcg_batch* bt, double tol, int maxit) {
+  BatchArgs a;
+  a.sys = bt->d_sys;
+  a.order = bt->d_order;
+  a.nsys = bt->nsys;
+  const long long T = bt->total;
+  a.b = bt->pool;
+  a.x = bt->pool + T;
+  a.r = bt->pool + 2 * T;
+  a.rt = bt->pool + 3 * T;
+  a.p = bt->pool + 4 * T;
+  a.s = bt->pool + 5 * T;
+  a.tol = tol;
+  a.maxit = maxit;
+  a.jacobi = bt->precond == PRCG_PRECOND_JACOBI;
+  a.iters = bt->d_iters;
+  a.status = bt->d_status;
+  a.queue = bt->d_queue;
+  return a;
+}
+
+cudaError_t launch_batched(prcg_batch* bt, const BatchArgs& a, cudaStream_t st) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3(bt->clusters * bt->cluster);
+  cfg.blockDim = dim3(bt->threads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = bt->cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_batched_pr, a);
+}
+
+// Persistent grid: as many clusters as can be resident at once.
+int size_grid(prcg_batch* bt) {
+  if (bt->cluster > 8)
+    BCK(cudaFuncSetAttribute(k_batched_pr, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3(bt->cluster);
+  cfg.blockDim = dim3(bt->threads);
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = bt->cluster;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nc = 0;
+  BCK(cudaOccupancyMaxActiveClusters(&nc, k_batched_pr, &cfg));
+  if (nc < 1) return berr(bt, PRCG_ERR_UNSUPPORTED, "cluster configuration cannot be resident");
+  bt->clusters = std::min(nc, bt->nsys);
+  return PRCG_OK;
+}
+
+void drop_graph(prcg_batch* bt) {
+  if (bt->exec) cudaGraphExecDestroy(bt->exec);
+  bt->exec = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int prcg_batched_create(prcg_batch** out, int nsys, const int32_t* nx, const int32_t* ny,
+                        const double* shift, int precond, void* cuda_stream) {
+  prcg_batch* bt = nullptr;
+  if (!out || nsys < 1 || !nx || !ny || !shift) return PRCG_ERR_INVALID;
+  if (precond != PRCG_PRECOND_NONE && precond != PRCG_PRECOND_JACOBI) return PRCG_ERR_INVALID;
+  *out = nullptr;
+  bt = new prcg_batch();
+  bt->nsys = nsys;
+  bt->precond = precond;
+  bt->user = (cudaStream_t)cuda_stream;
+  std::vector<BatchSys> sys(nsys);
+  std::vector<double> cost(nsys);
+  long long off = 0;
+  for (int i = 0; i < nsys; ++i) {
+    if (nx[i] < 1 || ny[i] < 1 || (long long)nx[i] * ny[i] >= (1LL << 30) || !(shift[i] >= 0.0) ||
+        !std::isfinite(shift[i])) {
+      delete bt;
+      return PRCG_ERR_INVALID;
+    }
+    sys[i].off = off;
+    sys[i].nx = nx[i];
+    sys[i].ny = ny[i];
+    sys[i].cdiag = 4.0 + shift[i];
+    sys[i].d = precond == PRCG_PRECOND_JACOBI ? 1.0 / sys[i].cdiag : 1.0;
+    const double n = (double)nx[i] * ny[i];
+    // work ~ n * sqrt(condition number): lambda_min of the shifted 5-point
+    // operator is 2 - 2 cos(pi/(nx+1)) + 2 - 2 cos(pi/(ny+1)) + shift
+    const double pi = 3.14159265358979323846;
+    const double lmin = 4.0 - 2.0 * cos(pi / (nx[i] + 1)) - 2.0 * cos(pi / (ny[i] + 1)) + shift[i];
+    cost[i] = n * sqrt((8.0 + shift[i]) / lmin);
+    off += (long long)nx[i] * ny[i];
+  }
+  bt->total = off;
+  std::vector<int> order(nsys);
+  for (int i = 0; i < nsys; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  if (cudaStreamCreateWithFlags(&bt->cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&bt->ev_user, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreate(&bt->ev0) != cudaSuccess || cudaEventCreate(&bt->ev1) != cudaSuccess ||
+      cudaMalloc(&bt->d_sys, nsys * sizeof(BatchSys)) != cudaSuccess ||
+      cudaMalloc(&bt->d_order, nsys * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&bt->d_iters, nsys * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&bt->d_status, nsys * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&bt->d_queue, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&bt->d_true, nsys * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&bt->pool, 6 * (size_t)off * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    prcg_batched_destroy(bt);
+    return PRCG_ERR_OOM;
+  }
+  cudaMemcpy(bt->d_sys, sys.data(), nsys * sizeof(BatchSys), cudaMemcpyHostToDevice);
+  cudaMemcpy(bt->d_order, order.data(), nsys * sizeof(int), cudaMemcpyHostToDevice);
+  if (size_grid(bt) != PRCG_OK) {
+    prcg_batched_destroy(bt);
+    return PRCG_ERR_CUDA;
+  }
+  *out = bt;
+  return PRCG_OK;
+}
+
+int prcg_batched_configure(prcg_batch* bt, int cluster, int threads) {
+  if (!bt) return PRCG_ERR_INVALID;
+  if (cluster < 1 || cluster > 16 || (cluster & (cluster - 1)) != 0)
+    return berr(bt, PRCG_ERR_INVALID, "cluster must be 1, 2, 4, 8 or 16");
+  if (threads < 64 || threads > kMaxThreads || threads % 32 != 0)
+    return berr(bt, PRCG_ERR_INVALID, "threads must be a multiple of 32 in [64, 1024]");
+  const int oc = bt->cluster, ot = bt->threads;
+  bt->cluster = cluster;
+  bt->threads = threads;
+  int rc = size_grid(bt);
+  if (rc != PRCG_OK) {
+    bt->cluster = oc;
+    bt->threads = ot;
+    size_grid(bt);
+    return rc;
+  }
+  drop_graph(bt);
+  return PRCG_OK;
+}
+
+int prcg_batched_solve(prcg_batch* bt, const double* b, double* x, double tol, int maxit,
+                       int32_t* iters_out, int32_t* status_out, double* true_relres_out) {
+  if (!bt || !b || !x) return PRCG_ERR_INVALID;
+  if (!(tol >= 0.0) || maxit < 0) return berr(bt, PRCG_ERR_INVALID, "tol < 0 or maxit < 0");
+  const size_t bytes = (size_t)bt->total * sizeof(double);
+  BatchArgs a = args_of(bt, tol, maxit);
+  BCK(cudaEventRecord(bt->ev_user, bt->user));
+  BCK(cudaStreamWaitEvent(bt->cs, bt->ev_user, 0));
+  BCK(cudaMemcpyAsync((void*)a.b, b, bytes, cudaMemcpyDefault, bt->cs));
+  BCK(cudaMemcpyAsync(a.x, x, bytes, cudaMemcpyDefault, bt->cs));
+  // one graph: reset the work queue, the persistent solver launch
+  if (bt->exec && (bt->graph_tol != tol || bt->graph_maxit != maxit)) drop_graph(bt);
+  if (!bt->exec) {
+    cudaGraph_t g = nullptr;
+    BCK(cudaStreamBeginCapture(bt->cs, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = cudaMemsetAsync(bt->d_queue, 0, sizeof(int), bt->cs);
+    if (e == cudaSuccess) e = launch_batched(bt, a, bt->cs);
+    cudaError_t e2 = cudaStreamEndCapture(bt->cs, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return berr(bt, PRCG_ERR_CUDA, std::string("batched graph capture: ") +
+                                          cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&bt->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return berr(bt, PRCG_ERR_CUDA, "batched graph instantiate");
+    bt->graph_tol = tol;
+    bt->graph_maxit = maxit;
+  }
+  BCK(cudaEventRecord(bt->ev0, bt->cs));
+  BCK(cudaGraphLaunch(bt->exec, bt->cs));
+  BCK(cudaEventRecord(bt->ev1, bt->cs));
+  if (true_relres_out) {
+    k_batched_true_res<<<std::min(bt->nsys, 1024), 256, 0, bt->cs>>>(a, bt->d_true);
+    BCK(cudaGetLastError());
+    BCK(cudaMemcpyAsync(true_relres_out, bt->d_true, bt->nsys * sizeof(double), cudaMemcpyDefault,
+                        bt->cs));
+  }
+  BCK(cudaMemcpyAsync(x, a.x, bytes, cudaMemcpyDefault, bt->cs));
+  if (iters_out)
+    BCK(cudaMemcpyAsync(iters_out, bt->d_iters, bt->nsys * sizeof(int), cudaMemcpyDefault, bt->cs));
+  std::vector<int> st(bt->nsys);
+  BCK(cudaMemcpyAsync(st.data(), bt->d_status, bt->nsys * sizeof(int), cudaMemcpyDeviceToHost,
+                      bt->cs));
+  BCK(cudaStreamSynchronize(bt->cs));
+  if (status_out) memcpy(status_out, st.data(), bt->nsys * sizeof(int));
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, bt->ev0, bt->ev1) == cudaSuccess) bt->last_ms = ms;
+  int worst = PRCG_OK;
+  for (int s : st) {
+    if (s < 0) return berr(bt, PRCG_ERR_CUDA, "a system finished without a status");
+    worst = std::max(worst, s);
+  }
+  return worst;
+}
+
+int prcg_batched_last_ms(const prcg_batch* bt, float* ms) {
+  if (!bt || !ms) return PRCG_ERR_INVALID;
+  *ms = bt->last_ms;
+  return PRCG_OK;
+}
+
+int prcg_batched_config(const prcg_batch* bt, int* cluster, int* threads, int* clusters) {
+  if (!bt) return PRCG_ERR_INVALID;
+  if (cluster) *cluster = bt->cluster;
+  if (threads) *threads = bt->threads;
+  if (clusters) *clusters = bt->clusters;
+  return PRCG_OK;
+}
+
+const char* prcg_batched_last_error(const prcg_batch* bt) { return bt ? bt->err.c_str() : ""; }
+
+int prcg_batched_destroy(prcg_batch* bt) {
+  if (!bt) return PRCG_OK;
+  if (bt->cs) cudaStreamSynchronize(bt->cs);
+  drop_graph(bt);
+  cudaFree(bt->d_sys);
+  cudaFree(bt->d_order);
+  cudaFree(bt->d_iters);
+  cudaFree(bt->d_status);
+  cudaFree(bt->d_queue);
+  cudaFree(bt->d_true);
+  cudaFree(bt->pool);
+  if (bt->ev_user) cudaEventDestroy(bt->ev_user);
+  if (bt->ev0) cudaEventDestroy(bt->ev0);
+  if (bt->ev1) cudaEventDestroy(bt->ev1);
+  if (bt->cs) cudaStreamDestroy(bt->cs);
+  delete bt;
+  return PRCG_OK;
+}
+
+}  // extern "C"
