@@ -339,6 +339,7 @@ def run_ours(args):
         line["e2e"] = run_e2e(G, S, prob, variant, tol, maxit, args)
         line["variants"] = run_variants(G, prob, S, b_dev, args)
         line["batched"] = run_batched(G, args)
+        line["mixed_precision"] = run_mixed(G, prob, args)
         if world == 1:
             line["cpu_baseline"] = run_cpu_baseline(prob, variant, precond, args)
     S.close()
@@ -455,6 +456,45 @@ def run_batched(G, args):
             "plain_fp64_path": {"solves_per_s": plain_rate,
                                 "sample": "every 4th system solved alone with prcg_solve "
                                           "(device time of init + loop), rate over the sample"}}
+
+
+def run_mixed(G, prob, args):
+    """FP32-inner / FP64-refinement vs plain FP64 PR-CG, both to a true
+    relative residual of 1e-8: 256^3 Poisson (stencil, Jacobi) and the
+    Strakos diagonal (n = 1e5, lambda in [1e-3, 1e3], rho = 0.8)."""
+    import torch
+    import problems as P
+    out = {}
+    b = torch.from_numpy(prob.b).cuda()
+    with G.Solver.from_stencil(prob.dims, precond="jacobi") as S:
+        S.solve_refined_fp32(b, tol=1e-8)
+        x, status, outer, inner, trr, hist, ms = S.solve_refined_fp32(b, tol=1e-8)
+        S.solve(b, variant="pr", tol=1e-8, maxit=20000)
+        r = S.solve(b, variant="pr", tol=1e-8, maxit=20000, true_relres=True)
+        err = float((x - r.x).norm() / r.x.norm())
+        out["poisson3d_256_stencil_jacobi"] = {
+            "mixed_ms": ms, "outer": outer, "inner_iters": inner, "true_relres": trr,
+            "fp64_ms": r.init_ms + r.loop_ms, "fp64_iters": r.iters, "fp64_true_relres": r.true_relres,
+            "speedup": (r.init_ms + r.loop_ms) / ms, "rel_diff_vs_fp64_solution": err,
+            "status": status}
+    lam, bs = P.strakos_diagonal(100000, 1e-3, 1e3, 0.8)
+    n = len(lam)
+    rp = np.arange(n + 1, dtype=np.int32)
+    ci = np.arange(n, dtype=np.int32)
+    bb = torch.from_numpy(bs).cuda()
+    xs = 1 / np.sqrt(n)
+    with G.Solver.from_csr(rp, ci, lam) as S:
+        S.solve_refined_fp32(bb, tol=1e-8)
+        x, status, outer, inner, trr, hist, ms = S.solve_refined_fp32(bb, tol=1e-8)
+        S.solve(bb, variant="pr", tol=1e-8, maxit=200000)
+        r = S.solve(bb, variant="pr", tol=1e-8, maxit=200000, true_relres=True)
+        out["strakos_diag_1e5"] = {
+            "mixed_ms": ms, "outer": outer, "inner_iters": inner, "true_relres": trr,
+            "err_vs_exact": float((x.cpu().numpy() - xs).__abs__().max() / xs),
+            "fp64_ms": r.init_ms + r.loop_ms, "fp64_iters": r.iters,
+            "fp64_err_vs_exact": float((r.x.cpu().numpy() - xs).__abs__().max() / xs),
+            "speedup": (r.init_ms + r.loop_ms) / ms, "status": status}
+    return out
 
 
 def oracle_sample(prob, variant, precond, iters):

@@ -125,6 +125,35 @@ int prcg_solve(prcg_ctx* ctx, int variant, const double* b, double* x,
                int* iters_out, double* final_true_relres_out);
 
 /*
+ * prcg_solve_f32_refined -- FP32 PR-CG inner solves inside FP64 iterative
+ * refinement (an extension; the paper's experiments are all FP64).
+ * Outer step j: t = b - A x_j in FP64; stop when ||t|| / ||b|| <= tol;
+ * otherwise solve A d = t / ||t|| by PR-CG (Algorithm 2) with FP32 vectors
+ * and FP32 matrix values to ||r|| <= max(inner_tol, min(0.5, tol / (4 ||t||
+ * / ||b||))) -- the last steps stop as soon as tol is within reach -- or
+ * inner_maxit iterations,
+ * inner products accumulated with compensated FP32 per thread and FP64
+ * across threads, alpha / beta / nu' recurrences in FP64; then
+ * x_{j+1} = x_j + ||t|| d in FP64.  The run also stops when an outer step
+ * does not reduce the true residual.
+ *   b, x            as prcg_solve (x: in x_0, out the refined solution)
+ *   tol             on the FP64 true residual ||b - A x|| / ||b||
+ *   max_outer       refinement steps (>= 0)
+ *   inner_tol       relative, in (0, 1); inner_maxit >= 1
+ *   outer_out, inner_total_out   NULL or the counts
+ *   final_true_relres_out        NULL or ||b - A x|| / ||b|| at return
+ *   outer_history   NULL or double[max_outer + 1]: true residual per step
+ * Returns PRCG_OK, PRCG_NOT_CONVERGED (max_outer reached or no progress),
+ * PRCG_BREAKDOWN (an inner solve made no iteration) or a negative error;
+ * PRCG_ERR_UNSUPPORTED for a context that kept the plain CSR layout.
+ * prcg_last_timing reports the whole solve as loop_ms.
+ */
+int prcg_solve_f32_refined(prcg_ctx* ctx, const double* b, double* x, double tol, int max_outer,
+                           double inner_tol, int inner_maxit, int* outer_out,
+                           int* inner_total_out, double* final_true_relres_out,
+                           double* outer_history);
+
+/*
  * prcg_last_timing -- device time of the last prcg_solve on this context,
  * measured with CUDA events around its phases on the context's stream:
  *   init_ms   initialisation (r_0 ... first reduction)

@@ -8,3 +8,4 @@ with it.  See ``cg_variants`` for the algorithms and ``adjoint`` /
 from .cg_variants import (OK, NOT_CONVERGED, BREAKDOWN, VARIANTS, SOLVERS, Result,  # noqa: F401
                           solve, hs_cg, pr_cg, pipe_pr_cg, m_cg, pipe_m_cg, cg_cg, gv_cg,
                           jacobi_inverse_diagonal, true_relres, a_norm_error, as_operator)
+from .refinement import refined_fp32  # noqa: F401,E402

@@ -87,6 +87,20 @@ class Solver:
         return SolveResult(x, iters, status, None if hist is None else hist[:iters + 1], trr,
                            init_ms, loop_ms)
 
+    def solve_refined_fp32(self, b, x0=None, tol: float = 1e-8, max_outer: int = 30,
+                           inner_tol: float = 1e-4, inner_maxit: Optional[int] = None):
+        """FP32 PR-CG inner solves + FP64 iterative refinement.  Returns
+        (x, status, outer steps, inner iterations, true relres, outer history, ms)."""
+        torch = _torch()
+        x = x0 if x0 is not None else torch.zeros(self.n, dtype=torch.float64, device="cuda")
+        if inner_maxit is None:
+            inner_maxit = 2 * self.n
+        hist = np.zeros(max_outer + 1)
+        status, outer, inner, trr = binding.prcg_solve_f32_refined(
+            self.handle, b, x, tol, max_outer, inner_tol, inner_maxit, hist)
+        _, loop_ms, _ = binding.prcg_last_timing(self.handle)
+        return x, status, outer, inner, trr, hist[:outer + 1], loop_ms
+
     def close(self):
         if self.handle:
             binding.prcg_destroy(self.handle)

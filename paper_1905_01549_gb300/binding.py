@@ -29,7 +29,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_INVALID", 
 
 # every symbol include/prcg.h declares
 EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_solve", "prcg_last_timing",
-           "prcg_time_sweeps",
+           "prcg_time_sweeps", "prcg_solve_f32_refined",
            "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n",
            "prcg_pr_solve_stencil_noalloc", "prcg_batched_create", "prcg_batched_configure",
            "prcg_batched_solve", "prcg_batched_last_ms", "prcg_batched_config",
@@ -70,6 +70,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.prcg_solve.restype = ctypes.c_int
     lib.prcg_last_timing.argtypes = [vp, _c_float_p, _c_float_p, _c_int_p]
     lib.prcg_last_timing.restype = ctypes.c_int
+    lib.prcg_solve_f32_refined.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int,
+                                           ctypes.c_double, ctypes.c_int, _c_int_p, _c_int_p,
+                                           _c_double_p, vp]
+    lib.prcg_solve_f32_refined.restype = ctypes.c_int
     lib.prcg_time_sweeps.argtypes = [vp, ctypes.c_int, ctypes.c_int, _c_float_p, _c_int_p]
     lib.prcg_time_sweeps.restype = ctypes.c_int
     lib.prcg_last_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
@@ -173,6 +177,16 @@ def prcg_last_timing(ctx):
     a, b, k = ctypes.c_float(), ctypes.c_float(), ctypes.c_int()
     _check(lib.prcg_last_timing(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(k)), ctx)
     return a.value, b.value, k.value
+
+
+def prcg_solve_f32_refined(ctx, b, x, tol, max_outer, inner_tol, inner_maxit, outer_history=None):
+    """FP32 inner / FP64 refinement solve; returns (status, outer, inner_total, true_relres)."""
+    o, it, trr = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    rc = load().prcg_solve_f32_refined(ctx, ptr(b), ptr(x), float(tol), int(max_outer),
+                                       float(inner_tol), int(inner_maxit), ctypes.byref(o),
+                                       ctypes.byref(it), ctypes.byref(trr), ptr(outer_history))
+    _check(rc, ctx)
+    return rc, o.value, it.value, trr.value
 
 
 def prcg_time_sweeps(ctx, variant, reps):

@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/prcg.h"
@@ -130,6 +131,12 @@ __global__ void k_fill(double* v, int n, double a) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = a;
 }
 
+__global__ void k_to_f32(const double* a, float* b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
 // Body-end control of the device-side while loop.
 __global__ void k_loop_control(cudaGraphConditionalHandle h, DevState* S) {
   const unsigned b = S->bodies + 1u;
@@ -186,6 +193,9 @@ struct prcg_ctx {
   int last_iters = 0;
   int64_t last_launches = 0;
   int64_t host_loop_launches = 0;
+  float* pool32 = nullptr;       // FP32 vectors of the mixed-precision inner solve
+  float* sval32 = nullptr;       // FP32 copy of the SELL values
+  DevState* S2 = nullptr;        // scalar block of the inner solve
   std::string err;
 };
 
@@ -336,15 +346,31 @@ int launch_iter(prcg_ctx* c, int variant, int qr, int qw, cudaStream_t st) {
 
 int chunk_for(prcg_ctx* c) { return c->n >= (1 << 20) ? 2 : 16; }
 
+constexpr int kMixedGraph = 7;   // graphs[7]: the FP32 inner solve of the mixed form
+
+int launch_mixed_init(prcg_ctx* c, cudaStream_t st) {
+  CK(c->launch(c->plan, PH_MX_INIT_A, 0, 0, 0, st));
+  CK(c->launch(c->plan, PH_MX_INIT_B, 0, 0, 0, st));
+  return PRCG_OK;
+}
+
+int launch_mixed_iter(prcg_ctx* c, cudaStream_t st) {
+  CK(c->launch(c->plan, PH_MX_PR_A, 0, 0, 0, st));
+  CK(c->launch(c->plan, PH_MX_PR_B, 0, 0, 0, st));
+  return PRCG_OK;
+}
+
 int build_graph(prcg_ctx* c, int variant) {
   VariantGraph& G = c->graphs[variant];
   if (G.exec) return PRCG_OK;
+  const bool mixed = variant == kMixedGraph;
+  DevState* SS = mixed ? c->S2 : c->S;
   const int chunk = chunk_for(c);
   cudaGraph_t g = nullptr;
   CK(cudaGraphCreate(&g, 0));
   G.graph = g;
   CK(cudaStreamBeginCaptureToGraph(c->cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  int rc = launch_init(c, variant, c->cs);
+  int rc = mixed ? launch_mixed_init(c, c->cs) : launch_init(c, variant, c->cs);
   if (rc == PRCG_OK) {
     cudaError_t e = cudaEventRecordWithFlags(c->ev_init, c->cs, cudaEventRecordExternal);
     if (e != cudaSuccess) rc = cuda_err(c, e, "event record in capture");
@@ -373,9 +399,10 @@ int build_graph(prcg_ctx* c, int variant) {
       e = cudaStreamBeginCaptureToGraph(c->bs, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) rc = cuda_err(c, e, "body capture");
-      for (int m = 0; rc == PRCG_OK && m < chunk; ++m) rc = launch_iter(c, variant, m & 1, (m + 1) & 1, c->bs);
+      for (int m = 0; rc == PRCG_OK && m < chunk; ++m)
+        rc = mixed ? launch_mixed_iter(c, c->bs) : launch_iter(c, variant, m & 1, (m + 1) & 1, c->bs);
       if (rc == PRCG_OK) {
-        k_loop_control<<<1, 1, 0, c->bs>>>(h, c->S);
+        k_loop_control<<<1, 1, 0, c->bs>>>(h, SS);
         e = cudaGetLastError();
         if (e != cudaSuccess) rc = cuda_err(c, e, "loop control launch");
       }
@@ -752,6 +779,121 @@ int prcg_time_sweeps(prcg_ctx* c, int variant, int reps, float* ms_per_sweep, in
   return PRCG_OK;
 }
 
+int prcg_solve_f32_refined(prcg_ctx* c, const double* b, double* x, double tol, int max_outer,
+                           double inner_tol, int inner_maxit, int* outer_out, int* inner_total_out,
+                           double* final_true_relres_out, double* outer_history) {
+  if (!c) return set_err(nullptr, PRCG_ERR_INVALID, "ctx is NULL");
+  if (!b || !x) return set_err(c, PRCG_ERR_INVALID, "b or x is NULL");
+  if (!(tol >= 0.0) || max_outer < 0 || !(inner_tol > 0.0) || inner_tol >= 1.0 || inner_maxit < 1)
+    return set_err(c, PRCG_ERR_INVALID, "bad tolerance or iteration limit");
+  const int n = c->n;
+  if (c->plan.op.kind == OP_CSR)
+    return set_err(c, PRCG_ERR_UNSUPPORTED, "mixed precision needs the SELL-32 layout");
+  if (!c->pool32) {
+    CK(cudaMalloc(&c->pool32, 6 * (size_t)n * sizeof(float)));
+    CK(cudaMalloc(&c->S2, sizeof(DevState)));
+    float* q = c->pool32;
+    Vecs32& W = c->plan.w;
+    W.r = q; W.rt = q + n; W.p = q + 2 * (size_t)n; W.s = q + 3 * (size_t)n;
+    W.d = q + 4 * (size_t)n; W.rhs = q + 5 * (size_t)n;
+    c->plan.S2 = c->S2;
+    if (c->plan.op.kind == OP_SELL) {
+      const int nslices = (n + 31) / 32;
+      int total = 0;
+      CK(cudaMemcpy(&total, c->plan.op.sptr + nslices, sizeof(int), cudaMemcpyDeviceToHost));
+      CK(cudaMalloc(&c->sval32, ((size_t)total + 4) * sizeof(float)));
+      k_to_f32<<<c->plan.sms * 8, 256, 0, c->cs>>>(c->plan.op.sval, c->sval32, total);
+      CK(cudaGetLastError());
+      c->plan.op.sval32 = c->sval32;
+    }
+  }
+  int rc;
+  if ((rc = wait_user(c)) != PRCG_OK) return rc;
+  if ((rc = copy_in(c, (void*)c->plan.v.b, b, (size_t)n * sizeof(double))) != PRCG_OK) return rc;
+  if ((rc = copy_in(c, c->plan.v.x, x, (size_t)n * sizeof(double))) != PRCG_OK) return rc;
+  bool graph = c->use_graph;
+  if (graph && build_graph(c, kMixedGraph) != PRCG_OK) graph = false;
+  CK(cudaMemsetAsync(c->S, 0, sizeof(DevState), c->cs));
+  CK(cudaEventRecord(c->ev_start, c->cs));
+  int status = PRCG_NOT_CONVERGED, outer = 0, inner_total = 0;
+  double rel = 0.0, prev = INFINITY;
+  int64_t launches = 0;
+  const int chunk = 16;
+  for (;;) {
+    CK(c->launch(c->plan, PH_MX_RESID, 0, 0, 0, c->cs));
+    ++launches;
+    DevState h;
+    CK(cudaMemcpyAsync(&h, c->S, sizeof h, cudaMemcpyDeviceToHost, c->cs));
+    CK(cudaStreamSynchronize(c->cs));
+    const double tn = sqrt(h.eta), bn = sqrt(h.nu_pred);
+    if (bn == 0.0) {
+      CK(cudaMemsetAsync(c->plan.v.x, 0, (size_t)n * sizeof(double), c->cs));
+      rel = 0.0;
+      status = PRCG_OK;
+      if (outer_history) outer_history[outer] = 0.0;
+      break;
+    }
+    rel = tn / bn;
+    if (outer_history) outer_history[outer] = rel;
+    if (rel <= tol) { status = PRCG_OK; break; }
+    if (outer >= max_outer || !(rel < prev)) { status = PRCG_NOT_CONVERGED; break; }
+    prev = rel;
+    // inner FP32 PR-CG on A d = t / ||t||, to inner_tol -- or, when less
+    // suffices to reach tol, to a quarter of the remaining reduction
+    DevState& hs = *c->hS;
+    memset(&hs, 0, sizeof hs);
+    hs.tol = std::max(inner_tol, std::min(0.5, 0.25 * tol / rel));
+    hs.maxit = inner_maxit;
+    hs.status = kRunning;
+    hs.arg = 1.0 / tn;
+    const int ichunk = chunk_for(c);
+    hs.maxbodies = inner_maxit / ichunk + 3;
+    CK(cudaMemcpyAsync(c->S2, &hs, sizeof hs, cudaMemcpyHostToDevice, c->cs));
+    DevState h2;
+    if (graph) {
+      CK(cudaGraphLaunch(c->graphs[kMixedGraph].exec, c->cs));
+      CK(cudaMemcpyAsync(&h2, c->S2, sizeof h2, cudaMemcpyDeviceToHost, c->cs));
+      CK(cudaStreamSynchronize(c->cs));
+      launches += 2 + (int64_t)h2.bodies * (2 * ichunk + 1);
+    } else {
+      if ((rc = launch_mixed_init(c, c->cs)) != PRCG_OK) return rc;
+      launches += 2;
+      for (int it = 0; it <= inner_maxit; it += chunk) {
+        CK(cudaMemcpyAsync(&h2, c->S2, sizeof h2, cudaMemcpyDeviceToHost, c->cs));
+        CK(cudaStreamSynchronize(c->cs));
+        if (h2.done) break;
+        for (int m = 0; m < chunk; ++m) {
+          if ((rc = launch_mixed_iter(c, c->cs)) != PRCG_OK) return rc;
+          launches += 2;
+        }
+      }
+      CK(cudaMemcpyAsync(&h2, c->S2, sizeof h2, cudaMemcpyDeviceToHost, c->cs));
+      CK(cudaStreamSynchronize(c->cs));
+    }
+    if (h2.status < 0) return set_err(c, h2.status, "inner loop exceeded its iteration limit");
+    inner_total += h2.k;
+    if (h2.k == 0) { status = PRCG_BREAKDOWN; break; }
+    c->plan.arg = tn;
+    CK(c->launch(c->plan, PH_MX_UPDATE, 0, 0, 0, c->cs));
+    ++launches;
+    ++outer;
+  }
+  CK(cudaEventRecord(c->ev_loop, c->cs));
+  CK(cudaMemcpyAsync(x, c->plan.v.x, (size_t)n * sizeof(double), cudaMemcpyDefault, c->cs));
+  CK(cudaStreamSynchronize(c->cs));
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, c->ev_start, c->ev_loop) != cudaSuccess) ms = -1.f;
+  cudaGetLastError();
+  c->t_init = 0.f;
+  c->t_loop = ms;
+  c->last_iters = inner_total;
+  c->last_launches = launches;
+  if (outer_out) *outer_out = outer;
+  if (inner_total_out) *inner_total_out = inner_total;
+  if (final_true_relres_out) *final_true_relres_out = rel;
+  return status;
+}
+
 int prcg_last_timing(const prcg_ctx* c, float* init_ms, float* loop_ms, int* iters) {
   if (!c) return PRCG_ERR_INVALID;
   if (init_ms) *init_ms = c->t_init;
@@ -774,6 +916,9 @@ int prcg_destroy(prcg_ctx* c) {
   if (c->ipool) cudaFree(c->ipool);
   if (c->vpool) cudaFree(c->vpool);
   if (c->sell_i) cudaFree(c->sell_i);
+  if (c->pool32) cudaFree(c->pool32);
+  if (c->sval32) cudaFree(c->sval32);
+  if (c->S2) cudaFree(c->S2);
   if (c->sell_v) cudaFree(c->sell_v);
   if (c->partials) cudaFree(c->partials);
   if (c->S) cudaFree(c->S);

@@ -39,6 +39,7 @@ struct DevState {
   unsigned arrive;       // CTAs that finished the current sweep
   unsigned bodies;       // executions of the while-loop body
   int profile;           // timing runs: never finish, keep every sweep doing its work
+  double arg;            // mixed precision: 1 / ||t|| of the current refinement step
 };
 
 // Pointers of one context; kernels take what they need by value.
@@ -53,6 +54,30 @@ struct Vecs {
   double* w[2];
   double* u[2];
   double* t;             // scratch vector (true residual, GV's t_k)
+};
+
+// FP32 vectors of the mixed-precision inner solve (A d = r in FP32).
+struct Vecs32 {
+  float* r;
+  float* rt;
+  float* p;
+  float* s;
+  float* d;      // the inner iterate (correction)
+  float* rhs;    // r_outer / ||r_outer||
+};
+
+// Compensated (Kahan) FP32 accumulator: inner products of the FP32 solve
+// accumulate their FP32 products without FP64 instructions; the running
+// error term keeps the sum accurate to about one FP32 rounding.
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = __fsub_rn(v, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
 __device__ __forceinline__ double ldcs(const double* p) { return __ldcs(p); }

@@ -12,3 +12,6 @@ LaunchFn launcher_csr(int op_kind, int pc_kind) {
 }
 
 }  // namespace prcg
+
+static_assert(prcg::HasRow32<prcg::SellOp>::value, "SELL-32 has an FP32 row");
+static_assert(!prcg::HasRow32<prcg::CsrOp>::value, "CSR has no FP32 row");

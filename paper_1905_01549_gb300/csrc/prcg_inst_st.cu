@@ -12,3 +12,5 @@ LaunchFn launcher_st(int op_kind, int pc_kind) {
 }
 
 }  // namespace prcg
+
+static_assert(prcg::HasRow32<prcg::StencilOp<3>>::value, "stencil has an FP32 row");

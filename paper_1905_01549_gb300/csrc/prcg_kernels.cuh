@@ -331,6 +331,163 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
   }
 }
 
+// ------------------------------------------------ mixed precision (FP32 inner)
+// Iterative refinement: the outer loop forms t = b - A x in FP64, scales it
+// to rhs = t / ||t|| in FP32, runs PR-CG on A d = rhs with FP32 vectors and
+// FP32 matrix values (inner products: FP32 products, compensated FP32
+// accumulation per thread, FP64 across threads; scalars alpha, beta, nu' in
+// FP64, rounded to FP32 only where a vector update applies them), and adds
+// x += ||t|| d in FP64.  S is the inner solve's own scalar block.
+
+// FP64 outer residual t = b - A x with ||t||^2, ||b||^2 into S->eta, S->nu_pred.
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_mx_resid(Op op, Pc pc, Vecs V, DevState* S,
+                                                     double* partials) {
+  double acc[2] = {0.0, 0.0};
+  const double* __restrict__ x = V.x;
+  PRCG_ROWS(i, op.n) {
+    const double bi = __ldg(V.b + i);
+    const double t = bi - op.row(i, [&](int j) { return __ldg(x + j); });
+    V.t[i] = t;
+    acc[0] = fma(t, t, acc[0]);
+    acc[1] = fma(bi, bi, acc[1]);
+  }
+  double tot[2];
+  if (grid_sum<2>(acc, partials, S, tot) && threadIdx.x == 0) {
+    S->eta = tot[0];
+    S->nu_pred = tot[1];
+  }
+}
+
+// rhs = t * inv_norm in FP32, and the inner solve's initialize() for d_0 = 0:
+// r_0 = rhs, r~_0 = M^{-1} r_0, p_0 = r~_0; nu_0, <r_0, r_0>, <rhs, rhs>.
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_mx_init_a(Op op, Pc pc, Vecs V, Vecs32 W, DevState* S,
+                                                      double* partials) {
+  const double inv_norm = __ldcg(&S->arg);
+  KahanF nu, rr;
+  PRCG_ROWS(i, op.n) {
+    const float ri = (float)(__ldg(V.t + i) * inv_norm);
+    const float rti = Pc::on ? (float)pc(i) * ri : ri;
+    W.rhs[i] = ri;
+    W.r[i] = ri;
+    W.rt[i] = rti;
+    W.p[i] = rti;
+    W.d[i] = 0.f;
+    nu.add(rti * ri);
+    rr.add(ri * ri);
+  }
+  double acc[2] = {nu.value(), rr.value()};
+  double tot[2];
+  if (grid_sum<2>(acc, partials, S, tot) && threadIdx.x == 0) {
+    S->nu = tot[0];
+    S->rho = tot[1];
+    S->bnorm2 = tot[1];
+    S->k = 0;
+    record_and_test(S, 0, tot[1]);
+  }
+}
+
+// s_0 = A p_0; mu_0, sigma_0, gamma_0; alpha_0, nu'_1, beta_1.
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_mx_init_b(Op op, Pc pc, Vecs32 W, DevState* S,
+                                                      double* partials) {
+  if (__ldcg(&S->done)) return;
+  KahanF mu, sg, ga;
+  const float* __restrict__ p = W.p;
+  PRCG_ROWS(i, op.n) {
+    const float sn = op.row32(i, [&](int j) { return __ldg(p + j); });
+    W.s[i] = sn;
+    mu.add(__ldg(p + i) * sn);
+    sg.add(__ldg(W.rt + i) * sn);
+    ga.add((Pc::on ? (float)pc(i) * sn : sn) * sn);
+  }
+  double acc[3] = {mu.value(), sg.value(), ga.value()};
+  double tot[3];
+  if (grid_sum<3>(acc, partials, S, tot) && threadIdx.x == 0) {
+    S->mu = tot[0];
+    S->sigma = tot[1];
+    S->gamma = tot[2];
+    scalar_step_pr(S, false);
+  }
+}
+
+// Sweep A of inner iteration k (FP32 vectors).
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_mx_pr_a(Op op, Pc pc, Vecs32 W, DevState* S,
+                                                    double* partials_a) {
+  if (__ldcg(&S->done)) return;
+  const float af = (float)__ldcg(&S->alpha);
+  const float bf = (float)__ldcg(&S->beta);
+  KahanF nu, rr;
+  PRCG_ROWS(i, op.n) {
+    const float si = W.s[i];
+    const float pi = W.p[i];
+    W.d[i] = fmaf(af, pi, W.d[i]);
+    const float rn = fmaf(-af, si, W.r[i]);
+    W.r[i] = rn;
+    float rtn = rn;
+    if (Pc::on) {
+      rtn = fmaf(-af, (float)pc(i) * si, W.rt[i]);
+      W.rt[i] = rtn;
+    }
+    W.p[i] = fmaf(bf, pi, rtn);
+    nu.add(rtn * rn);
+    rr.add(rn * rn);
+  }
+  double acc[2] = {Pc::on ? nu.value() : rr.value(), rr.value()};
+  __shared__ double sm[2 * 32];
+  block_sum<2>(acc, sm);
+  if (threadIdx.x == 0) {
+    partials_a[blockIdx.x * 2 + 0] = acc[0];
+    partials_a[blockIdx.x * 2 + 1] = acc[1];
+  }
+}
+
+// Sweep B of inner iteration k: s_k = A p_k (FP32), mu, sigma, gamma; the
+// reduction adds sweep A's sums and forms the next FP64 scalars.
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_mx_pr_b(Op op, Pc pc, Vecs32 W, DevState* S,
+                                                    double* partials, const double* partials_a,
+                                                    int grid_a) {
+  if (__ldcg(&S->done)) return;
+  KahanF mu, sg, ga;
+  const float* __restrict__ p = W.p;
+  const float* __restrict__ rt = Pc::on ? W.rt : W.r;
+  PRCG_ROWS(i, op.n) {
+    const float sn = op.row32(i, [&](int j) { return __ldg(p + j); });
+    W.s[i] = sn;
+    mu.add(__ldg(p + i) * sn);
+    sg.add(__ldg(rt + i) * sn);
+    ga.add((Pc::on ? (float)pc(i) * sn : sn) * sn);
+  }
+  double acc[3] = {mu.value(), sg.value(), ga.value()};
+  double tot[3];
+  if (!grid_sum<3>(acc, partials, S, tot)) return;
+  double a2[2] = {0.0, 0.0};
+  for (int b = threadIdx.x; b < grid_a; b += blockDim.x) {
+    a2[0] += __ldcg(&partials_a[b * 2 + 0]);
+    a2[1] += __ldcg(&partials_a[b * 2 + 1]);
+  }
+  __shared__ double sm2[2 * 32];
+  block_sum<2>(a2, sm2);
+  if (threadIdx.x == 0) {
+    const int k = S->k + 1;
+    S->mu = tot[0];
+    S->sigma = tot[1];
+    S->gamma = tot[2];
+    S->nu = a2[0];
+    S->rho = a2[1];
+    if (!record_and_test(S, k, a2[1])) scalar_step_pr(S, false);
+  }
+}
+
+// x += scale * d (FP64 refinement update).
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_mx_update(Op op, Vecs V, Vecs32 W, double scale) {
+  PRCG_ROWS(i, op.n) { V.x[i] = fma(scale, (double)W.d[i], V.x[i]); }
+}
+
 // ---------------------------------------------------------------- helpers
 // ||b - A x||^2 and ||b||^2 into S->eta and S->nu_pred (after the run).
 template <class Op, class Pc>

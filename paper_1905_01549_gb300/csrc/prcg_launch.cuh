@@ -16,7 +16,13 @@ enum Phase {
   PH_PR_A = 5,
   PH_PR_B = 6,
   PH_PIPE = 7,
-  PH_TRUE_RES = 8
+  PH_TRUE_RES = 8,
+  PH_MX_RESID = 9,
+  PH_MX_INIT_A = 10,
+  PH_MX_INIT_B = 11,
+  PH_MX_PR_A = 12,
+  PH_MX_PR_B = 13,
+  PH_MX_UPDATE = 14
 };
 
 struct Plan {
@@ -27,6 +33,11 @@ struct Plan {
   double* partials;
   double* partials_a;    // PR sweep A's per-CTA sums
   int sms;
+  // mixed precision: FP32 vectors, the inner solve's scalar block and the
+  // scalar argument of the phase being launched (1 / ||t|| or ||t||)
+  Vecs32 w;
+  DevState* S2;
+  double arg;
 };
 
 using LaunchFn = cudaError_t (*)(const Plan&, int phase, int variant, int qr, int qw,
@@ -46,6 +57,55 @@ inline int grid_for(K kernel, int n, int sms) {
   if (g > kMaxGrid) g = kMaxGrid;
   if (g < 1) g = 1;
   return (int)g;
+}
+
+// FP32 inner-solve phases; operators without an FP32 row are not supported.
+template <class Op, class = void>
+struct HasRow32 : std::false_type {};
+template <class Op>
+struct HasRow32<Op, decltype((void)&Op::template row32<float (*)(int)>)> : std::true_type {};
+
+template <class Op, class Pc>
+cudaError_t launch_mixed(const Plan& P, int phase, cudaStream_t st) {
+  if constexpr (!HasRow32<Op>::value) {
+    return cudaErrorNotSupported;
+  } else {
+    Op op(P.op);
+    Pc pc(P.pc);
+    const int n = P.op.n;
+    double* pa = P.partials_a;
+    switch (phase) {
+      case PH_MX_INIT_A: {
+        auto k = k_mx_init_a<Op, Pc>;
+        k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.w, P.S2, P.partials);
+        break;
+      }
+      case PH_MX_INIT_B: {
+        auto k = k_mx_init_b<Op, Pc>;
+        k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.w, P.S2, P.partials);
+        break;
+      }
+      case PH_MX_PR_A: {
+        auto k = k_mx_pr_a<Op, Pc>;
+        k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.w, P.S2, pa);
+        break;
+      }
+      case PH_MX_PR_B: {
+        auto k = k_mx_pr_b<Op, Pc>;
+        const int grid_a = grid_for(k_mx_pr_a<Op, Pc>, n, P.sms);
+        k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.w, P.S2, P.partials, pa, grid_a);
+        break;
+      }
+      case PH_MX_UPDATE: {
+        auto k = k_mx_update<Op, Pc>;
+        k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, P.v, P.w, P.arg);
+        break;
+      }
+      default:
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
 }
 
 template <class Op, class Pc>
@@ -102,6 +162,17 @@ cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, 
       k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);
       break;
     }
+    case PH_MX_RESID: {
+      auto k = k_mx_resid<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);
+      break;
+    }
+    case PH_MX_INIT_A:
+    case PH_MX_INIT_B:
+    case PH_MX_PR_A:
+    case PH_MX_PR_B:
+    case PH_MX_UPDATE:
+      return launch_mixed<Op, Pc>(P, phase, st);
     default:
       return cudaErrorInvalidValue;
   }

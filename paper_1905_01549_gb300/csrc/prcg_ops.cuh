@@ -33,6 +33,7 @@ struct OpDesc {
   const int* slen;       // SELL-32: entries per row in each slice
   const int* scol;       // SELL-32 column indices, slice-major, row-minor
   const double* sval;    // SELL-32 values (padding: column = row, value 0)
+  const float* sval32;   // FP32 copy of sval for the mixed-precision inner solve
 };
 
 struct PcDesc {
@@ -82,7 +83,19 @@ struct SellOp {
   const int* __restrict__ scol;
   const double* __restrict__ sval;
   int n;
-  explicit SellOp(const OpDesc& o) : sptr(o.sptr), slen(o.slen), scol(o.scol), sval(o.sval), n(o.n) {}
+  const float* __restrict__ sval32;
+  explicit SellOp(const OpDesc& o)
+      : sptr(o.sptr), slen(o.slen), scol(o.scol), sval(o.sval), n(o.n), sval32(o.sval32) {}
+  // FP32 product row for the mixed-precision inner solve (FP32 values)
+  template <class G>
+  __device__ __forceinline__ float row32(int i, G&& g) const {
+    const int sl = i >> 5;
+    const int base = __ldg(sptr + sl) + (i & 31);
+    const int L = __ldg(slen + sl);
+    float acc = 0.f;
+    for (int t = 0; t < L; ++t) acc = fmaf(__ldg(sval32 + base + 32 * t), g(__ldg(scol + base + 32 * t)), acc);
+    return acc;
+  }
   // Entries t < 8 are loaded with predication (all loads of a row are in
   // flight together); longer rows continue in a plain loop.
   template <class F>
@@ -153,6 +166,12 @@ struct StencilOp {
     visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
     return acc;
   }
+  template <class G>
+  __device__ __forceinline__ float row32(int i, G&& g) const {
+    float acc = 0.f;
+    visit(i, [&](int j, double a) { acc = fmaf((float)a, g(j), acc); });
+    return acc;
+  }
   template <class G1, class G2>
   __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
     double c1 = 0.0, c2 = 0.0;
@@ -202,6 +221,12 @@ struct VarStencilOp {
   __device__ __forceinline__ double row(int i, G&& g) const {
     double acc = 0.0;
     visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
+    return acc;
+  }
+  template <class G>
+  __device__ __forceinline__ float row32(int i, G&& g) const {
+    float acc = 0.f;
+    visit(i, [&](int j, double a) { acc = fmaf((float)a, g(j), acc); });
     return acc;
   }
   template <class G1, class G2>
