@@ -340,6 +340,7 @@ def run_ours(args):
         line["variants"] = run_variants(G, prob, S, b_dev, args)
         line["batched"] = run_batched(G, args)
         line["mixed_precision"] = run_mixed(G, prob, args)
+        line["autograd"] = run_autograd(G, args)
         if world == 1:
             line["cpu_baseline"] = run_cpu_baseline(prob, variant, precond, args)
     S.close()
@@ -495,6 +496,36 @@ def run_mixed(G, prob, args):
             "fp64_err_vs_exact": float((r.x.cpu().numpy() - xs).__abs__().max() / xs),
             "speedup": (r.init_ms + r.loop_ms) / ms, "status": status}
     return out
+
+
+def run_autograd(G, args):
+    """Differentiation workload: 2D log-normal diffusion 512^2 (sigma = 2),
+    loss = ||x - x_t||^2, gradients w.r.t. b and every face coefficient via
+    the adjoint PR-CG solve (forward + backward to 1e-10, Jacobi)."""
+    import torch
+    import problems as P
+    from paper_1905_01549_gb300.autograd import DiffusionSolver
+    prob = P.varcoef2d(512, rhs="uniform", with_csr=False)
+    xt = torch.tensor(P.rng_for("grad512_xt").standard_normal(prob.n), device="cuda")
+    D = DiffusionSolver(prob.dims, precond="jacobi")
+    ff = torch.tensor(prob.face_array(), device="cuda")
+    bb = torch.tensor(prob.b, device="cuda")
+    times = []
+    for rep in range(3):
+        fc = ff.clone().requires_grad_(True)
+        bc = bb.clone().requires_grad_(True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x = D(fc, bc, tol=1e-10)
+        ((x - xt) ** 2).sum().backward()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    res = D.solver.solve(bb, variant="pr", tol=1e-10, maxit=10 ** 6)
+    D.close()
+    return {"workload": "varcoef2d_512 sigma=2, loss=||x-x_t||^2, d/db and d/dfaces",
+            "fwd_bwd_ms": min(times) * 1e3, "forward_iters": res.iters,
+            "faces": int(ff.numel()), "grad_norm_faces": float(fc.grad.norm()),
+            "grad_norm_b": float(bc.grad.norm())}
 
 
 def oracle_sample(prob, variant, precond, iters):

@@ -153,6 +153,28 @@ int prcg_solve_f32_refined(prcg_ctx* ctx, const double* b, double* x, double tol
                            int* inner_total_out, double* final_true_relres_out,
                            double* outer_history);
 
+/* ------------------------------------------------------------------------
+ * Adjoint gradients (an extension for differentiable use; the paper has no
+ * gradients).  For x = A^{-1} b and a loss L(x), with lambda = A^{-1} dL/dx
+ * (A is symmetric, so this is a second prcg_solve on the same context):
+ * dL/db = lambda and dL/dA = -lambda x^T on the stored entries.
+ * ------------------------------------------------------------------------ */
+
+/* Replace the face coefficients (same grid and layout as at creation) and the
+ * diagonal shift of a variable-coefficient stencil context; the diagonal and
+ * the Jacobi vector are recomputed. */
+int prcg_update_faces(prcg_ctx* ctx, const double* face_coeff, double diag_shift);
+
+/* grad_faces[f] = -(lambda_a - lambda_b)(x_a - x_b) for the interior face f
+ * between cells a and b, -lambda_a x_a for a boundary face of cell a, in the
+ * face layout of prcg_create_stencil.  lambda, x: double[n]; all host or
+ * device. */
+int prcg_grad_faces(prcg_ctx* ctx, const double* lambda, const double* x, double* grad_faces);
+
+/* grad_vals[e] = -lambda_i x_{col_idx[e]} for every stored entry e of row i,
+ * in the caller's CSR order (CSR contexts only). */
+int prcg_grad_csr_values(prcg_ctx* ctx, const double* lambda, const double* x, double* grad_vals);
+
 /*
  * prcg_last_timing -- device time of the last prcg_solve on this context,
  * measured with CUDA events around its phases on the context's stream:

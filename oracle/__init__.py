@@ -9,3 +9,4 @@ from .cg_variants import (OK, NOT_CONVERGED, BREAKDOWN, VARIANTS, SOLVERS, Resul
                           solve, hs_cg, pr_cg, pipe_pr_cg, m_cg, pipe_m_cg, cg_cg, gv_cg,
                           jacobi_inverse_diagonal, true_relres, a_norm_error, as_operator)
 from .refinement import refined_fp32  # noqa: F401,E402
+from . import adjoint  # noqa: F401,E402

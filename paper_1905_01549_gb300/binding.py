@@ -29,7 +29,8 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_INVALID", 
 
 # every symbol include/prcg.h declares
 EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_solve", "prcg_last_timing",
-           "prcg_time_sweeps", "prcg_solve_f32_refined",
+           "prcg_time_sweeps", "prcg_solve_f32_refined", "prcg_update_faces",
+           "prcg_grad_faces", "prcg_grad_csr_values",
            "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n",
            "prcg_pr_solve_stencil_noalloc", "prcg_batched_create", "prcg_batched_configure",
            "prcg_batched_solve", "prcg_batched_last_ms", "prcg_batched_config",
@@ -74,6 +75,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                            ctypes.c_double, ctypes.c_int, _c_int_p, _c_int_p,
                                            _c_double_p, vp]
     lib.prcg_solve_f32_refined.restype = ctypes.c_int
+    lib.prcg_update_faces.argtypes = [vp, vp, ctypes.c_double]
+    lib.prcg_update_faces.restype = ctypes.c_int
+    lib.prcg_grad_faces.argtypes = [vp, vp, vp, vp]
+    lib.prcg_grad_faces.restype = ctypes.c_int
+    lib.prcg_grad_csr_values.argtypes = [vp, vp, vp, vp]
+    lib.prcg_grad_csr_values.restype = ctypes.c_int
     lib.prcg_time_sweeps.argtypes = [vp, ctypes.c_int, ctypes.c_int, _c_float_p, _c_int_p]
     lib.prcg_time_sweeps.restype = ctypes.c_int
     lib.prcg_last_launches.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
@@ -187,6 +194,18 @@ def prcg_solve_f32_refined(ctx, b, x, tol, max_outer, inner_tol, inner_maxit, ou
                                        ctypes.byref(it), ctypes.byref(trr), ptr(outer_history))
     _check(rc, ctx)
     return rc, o.value, it.value, trr.value
+
+
+def prcg_update_faces(ctx, face_coeff, diag_shift=0.0):
+    return _check(load().prcg_update_faces(ctx, ptr(face_coeff), float(diag_shift)), ctx)
+
+
+def prcg_grad_faces(ctx, lam, x, grad_faces):
+    return _check(load().prcg_grad_faces(ctx, ptr(lam), ptr(x), ptr(grad_faces)), ctx)
+
+
+def prcg_grad_csr_values(ctx, lam, x, grad_vals):
+    return _check(load().prcg_grad_csr_values(ctx, ptr(lam), ptr(x), ptr(grad_vals)), ctx)
 
 
 def prcg_time_sweeps(ctx, variant, reps):

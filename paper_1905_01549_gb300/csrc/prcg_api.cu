@@ -131,6 +131,55 @@ __global__ void k_fill(double* v, int n, double a) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = a;
 }
 
+// Adjoint gradient of the face coefficients: for x = A^{-1} b and lambda =
+// A^{-1} dL/dx, dL/dc_f = -(lambda_a - lambda_b)(x_a - x_b) for the interior
+// face between cells a and b, and -lambda_a x_a for a boundary face of cell a.
+__global__ void k_grad_faces(int dim, int nx, int ny, int nz, const double* lam, const double* x,
+                             double* g) {
+  const long long nfx = (long long)nz * ny * (nx + 1);
+  const long long nfy = (long long)nz * (ny + 1) * nx;
+  const long long nfz = dim == 3 ? (long long)(nz + 1) * ny * nx : 0;
+  const long long nf = nfx + nfy + nfz;
+  for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf;
+       f += (long long)gridDim.x * blockDim.x) {
+    long long a = -1, b = -1;
+    if (f < nfx) {
+      const long long fx = f % (nx + 1), yz = f / (nx + 1);
+      const long long base = yz * nx;
+      if (fx > 0) a = base + fx - 1;
+      if (fx < nx) b = base + fx;
+    } else if (f < nfx + nfy) {
+      const long long q = f - nfx;
+      const long long x0 = q % nx, t = q / nx, fy = t % (ny + 1), z = t / (ny + 1);
+      if (fy > 0) a = (z * ny + fy - 1) * nx + x0;
+      if (fy < ny) b = (z * ny + fy) * nx + x0;
+    } else {
+      const long long q = f - nfx - nfy;
+      const long long pl = (long long)nx * ny;
+      const long long fz = q / pl, xy = q % pl;
+      if (fz > 0) a = (fz - 1) * pl + xy;
+      if (fz < nz) b = fz * pl + xy;
+    }
+    double v;
+    if (a >= 0 && b >= 0)
+      v = -(lam[a] - lam[b]) * (x[a] - x[b]);
+    else {
+      const long long c = a >= 0 ? a : b;
+      v = -lam[c] * x[c];
+    }
+    g[f] = v;
+  }
+}
+
+// dL/da_ij = -lambda_i x_j for every stored entry (caller's CSR order).
+__global__ void k_grad_csr(const int* rp, const int* ci, int n, const double* lam, const double* x,
+                           double* g) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double li = lam[i];
+    for (int e = rp[i]; e < rp[i + 1]; ++e) g[e] = -li * x[ci[e]];
+  }
+}
+
 __global__ void k_to_f32(const double* a, float* b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
@@ -892,6 +941,81 @@ int prcg_solve_f32_refined(prcg_ctx* c, const double* b, double* x, double tol, 
   if (inner_total_out) *inner_total_out = inner_total;
   if (final_true_relres_out) *final_true_relres_out = rel;
   return status;
+}
+
+int prcg_update_faces(prcg_ctx* c, const double* face_coeff, double diag_shift) {
+  if (!c || !face_coeff) return set_err(c, PRCG_ERR_INVALID, "NULL argument");
+  OpDesc& op = c->plan.op;
+  if (op.kind != OP_VC2 && op.kind != OP_VC3)
+    return set_err(c, PRCG_ERR_INVALID, "context has no face coefficients");
+  if (!(diag_shift >= 0.0) || !std::isfinite(diag_shift))
+    return set_err(c, PRCG_ERR_INVALID, "diag_shift must be finite and >= 0");
+  const int dim = op.kind == OP_VC2 ? 2 : 3;
+  const size_t nf = (size_t)op.nz * op.ny * (op.nx + 1) + (size_t)op.nz * (op.ny + 1) * op.nx +
+                    (dim == 3 ? (size_t)(op.nz + 1) * op.ny * op.nx : 0);
+  int rc;
+  if ((rc = wait_user(c)) != PRCG_OK) return rc;
+  if ((rc = copy_in(c, const_cast<double*>(op.fx), face_coeff, nf * sizeof(double))) != PRCG_OK) return rc;
+  double* d = c->plan.pc.kind == PC_VEC ? const_cast<double*>(c->plan.pc.d) : nullptr;
+  k_vc_diag<<<c->plan.sms * 4, 256, 0, c->cs>>>(dim, op.nx, op.ny, op.nz, op.fx, op.fy, op.fz,
+                                               diag_shift, const_cast<double*>(op.adiag), d, c->dbad);
+  return check_bad(c, "Jacobi needs a positive diagonal");
+}
+
+int prcg_grad_faces(prcg_ctx* c, const double* lambda, const double* x, double* grad_faces) {
+  if (!c || !lambda || !x || !grad_faces) return set_err(c, PRCG_ERR_INVALID, "NULL argument");
+  const OpDesc& op = c->plan.op;
+  if (op.kind != OP_VC2 && op.kind != OP_VC3)
+    return set_err(c, PRCG_ERR_INVALID, "context has no face coefficients");
+  const int dim = op.kind == OP_VC2 ? 2 : 3;
+  const size_t n = (size_t)c->n;
+  const size_t nf = (size_t)op.nz * op.ny * (op.nx + 1) + (size_t)op.nz * (op.ny + 1) * op.nx +
+                    (dim == 3 ? (size_t)(op.nz + 1) * op.ny * op.nx : 0);
+  int rc;
+  if ((rc = wait_user(c)) != PRCG_OK) return rc;
+  // lambda -> t, x -> the x buffer; the gradient is formed in the scratch s buffers
+  if ((rc = copy_in(c, c->plan.v.t, lambda, n * sizeof(double))) != PRCG_OK) return rc;
+  if ((rc = copy_in(c, c->plan.v.x, x, n * sizeof(double))) != PRCG_OK) return rc;
+  double* g = c->plan.v.r[1];   // r[1] .. u[1]: 7 contiguous scratch vectors, >= the faces
+  if (nf > 7 * n) return set_err(c, PRCG_ERR_INVALID, "internal: face gradient does not fit");
+  k_grad_faces<<<c->plan.sms * 8, 256, 0, c->cs>>>(dim, op.nx, op.ny, op.nz, c->plan.v.t,
+                                                  c->plan.v.x, g);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(grad_faces, g, nf * sizeof(double), cudaMemcpyDefault, c->cs));
+  CK(cudaStreamSynchronize(c->cs));
+  return PRCG_OK;
+}
+
+int prcg_grad_csr_values(prcg_ctx* c, const double* lambda, const double* x, double* grad_vals) {
+  if (!c || !lambda || !x || !grad_vals) return set_err(c, PRCG_ERR_INVALID, "NULL argument");
+  const OpDesc& op = c->plan.op;
+  if (!op.rp) return set_err(c, PRCG_ERR_INVALID, "context is not a CSR matrix");
+  const size_t n = (size_t)c->n;
+  int nnz = 0;
+  CK(cudaMemcpy(&nnz, op.rp + n, sizeof(int), cudaMemcpyDeviceToHost));
+  int rc;
+  if ((rc = wait_user(c)) != PRCG_OK) return rc;
+  if ((rc = copy_in(c, c->plan.v.t, lambda, n * sizeof(double))) != PRCG_OK) return rc;
+  if ((rc = copy_in(c, c->plan.v.x, x, n * sizeof(double))) != PRCG_OK) return rc;
+  double* g = nullptr;
+  const bool direct = [&] {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, grad_vals) != cudaSuccess) { cudaGetLastError(); return false; }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  }();
+  if (direct) {
+    g = grad_vals;
+  } else {
+    CK(cudaMalloc(&g, (size_t)nnz * sizeof(double)));
+  }
+  k_grad_csr<<<c->plan.sms * 4, 256, 0, c->cs>>>(op.rp, op.ci, (int)n, c->plan.v.t, c->plan.v.x, g);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && !direct)
+    e = cudaMemcpyAsync(grad_vals, g, (size_t)nnz * sizeof(double), cudaMemcpyDeviceToHost, c->cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->cs);
+  if (!direct) cudaFree(g);
+  if (e != cudaSuccess) return cuda_err(c, e, "CSR value gradient");
+  return PRCG_OK;
 }
 
 int prcg_last_timing(const prcg_ctx* c, float* init_ms, float* loop_ms, int* iters) {
