@@ -531,12 +531,14 @@ int build_sell(prcg_ctx* c) {
   int nnz = 0;
   CK(cudaMemcpy(&nnz, op.rp + n, sizeof(int), cudaMemcpyDeviceToHost));
   if (total > 2 * (int64_t)nnz + 64 * (int64_t)nslices) return PRCG_OK;  // too much padding
-  const size_t ni = (size_t)(nslices + 1) + (size_t)nslices + (size_t)total + 4;
+  // columns start on a 128-byte boundary: TMA copies whole tiles of them
+  const size_t col_off = ((size_t)(2 * nslices + 1) + 31) / 32 * 32;
+  const size_t ni = col_off + (size_t)total + 4;
   CK(cudaMalloc(&c->sell_i, ni * sizeof(int)));
   CK(cudaMalloc(&c->sell_v, ((size_t)total + 2) * sizeof(double)));
   int* sptr_d = c->sell_i;
   int* slen2_d = c->sell_i + nslices + 1;
-  int* scol_d = slen2_d + nslices;
+  int* scol_d = c->sell_i + col_off;
   CK(cudaMemcpyAsync(sptr_d, sptr.data(), (size_t)(nslices + 1) * sizeof(int),
                      cudaMemcpyHostToDevice, c->cs));
   CK(cudaMemcpyAsync(slen2_d, slen.data(), (size_t)nslices * sizeof(int), cudaMemcpyHostToDevice,
@@ -550,6 +552,8 @@ int build_sell(prcg_ctx* c) {
   op.scol = scol_d;
   op.sval = c->sell_v;
   op.kind = OP_SELL;
+  const char* nt = getenv("PRCG_NO_TMA");
+  op.tma = (!(nt && nt[0] == '1') && sell_fits_tma(sptr.data(), nslices)) ? 1 : 0;
   return PRCG_OK;
 }
 

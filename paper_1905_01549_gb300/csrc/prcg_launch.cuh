@@ -3,7 +3,7 @@
 // library compiles in parallel translation units.
 #pragma once
 
-#include "prcg_kernels.cuh"
+#include "prcg_tma.cuh"
 
 namespace prcg {
 
@@ -136,6 +136,13 @@ cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, 
       break;
     }
     case PH_HS_C: {
+      if constexpr (std::is_same<Op, SellOp>::value) {
+        if (P.op.tma) {
+          auto kt = k_hs_c_tma<Pc>;
+          kt<<<grid_for(kt, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);
+          break;
+        }
+      }
       auto k = k_hs_c<Op, Pc>;
       k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);
       break;
@@ -146,13 +153,29 @@ cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, 
       break;
     }
     case PH_PR_B: {
-      auto k = k_pr_b<Op, Pc>;
       const int grid_a = grid_for(k_pr_a<Op, Pc>, n, P.sms);
+      if constexpr (std::is_same<Op, SellOp>::value) {
+        if (P.op.tma) {
+          auto kt = k_pr_b_tma<Pc>;
+          kt<<<grid_for(kt, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, P.partials_a,
+                                                         grid_a, meurant);
+          break;
+        }
+      }
+      auto k = k_pr_b<Op, Pc>;
       k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, P.partials_a,
                                                    grid_a, meurant);
       break;
     }
     case PH_PIPE: {
+      if constexpr (std::is_same<Op, SellOp>::value) {
+        if (P.op.tma) {
+          auto kt = k_pipe_tma<Pc>;
+          kt<<<grid_for(kt, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw,
+                                                         meurant);
+          break;
+        }
+      }
       auto k = k_pipe<Op, Pc>;
       k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw, meurant);
       break;

@@ -34,6 +34,7 @@ struct OpDesc {
   const int* scol;       // SELL-32 column indices, slice-major, row-minor
   const double* sval;    // SELL-32 values (padding: column = row, value 0)
   const float* sval32;   // FP32 copy of sval for the mixed-precision inner solve
+  int tma;               // SELL-32 tiles fit the TMA stages: product sweeps stage entries in smem
 };
 
 struct PcDesc {
