@@ -15,7 +15,9 @@
  *   PRCG_PIPE_PR  pipe-PR-CG, Algorithm 3 -- s, s~ from the predicted w',
  *                 u = A s~ and w = A r~ (recomputed) in one pass over A
  *                 together with the four inner products
- *   PRCG_M, PRCG_PIPE_M, PRCG_CGCG, PRCG_GV are the Appendix E variants.
+ *   PRCG_M, PRCG_PIPE_M, PRCG_CGCG, PRCG_GV are the Appendix E variants
+ *                 (M-CG, pipe-PR-M-CG, Chronopoulos-Gear CG in 2 sweeps,
+ *                 Ghysels-Vanroose pipelined CG in 1 sweep per iteration).
  *
  * Threading: a context is not thread-safe; use one context per host thread.
  * All work of a context runs on the CUDA stream given at creation (or the

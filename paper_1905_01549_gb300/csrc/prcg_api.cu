@@ -364,7 +364,8 @@ int iter_launches(int variant) {
   switch (variant) {
     case V_HS: return 3;
     case V_PR:
-    case V_M: return 2;
+    case V_M:
+    case V_CGCG: return 2;
     default: return 1;
   }
 }
@@ -386,6 +387,13 @@ int launch_iter(prcg_ctx* c, int variant, int qr, int qw, cudaStream_t st) {
     case V_PIPE:
     case V_PIPE_M:
       CK(c->launch(c->plan, PH_PIPE, variant, qr, qw, st));
+      break;
+    case V_CGCG:
+      CK(c->launch(c->plan, PH_CG_A, variant, qr, qw, st));
+      CK(c->launch(c->plan, PH_CG_B, variant, qr, qw, st));
+      break;
+    case V_GV:
+      CK(c->launch(c->plan, PH_GV, variant, qr, qw, st));
       break;
     default:
       return set_err(c, PRCG_ERR_UNSUPPORTED, "variant not built on the GPU path");
@@ -701,8 +709,6 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   if (!b || !x) return set_err(c, PRCG_ERR_INVALID, "b or x is NULL");
   if (!(tol >= 0.0) || maxit < 0) return set_err(c, PRCG_ERR_INVALID, "tol < 0 or maxit < 0");
   if (variant < 0 || variant > 6) return set_err(c, PRCG_ERR_INVALID, "unknown variant");
-  if (variant == V_CGCG || variant == V_GV)
-    return set_err(c, PRCG_ERR_UNSUPPORTED, "CG-CG and GV-CG are not built on the GPU path");
   const int n = c->n;
   int rc;
   if (c->hist_cap < maxit + 1) {
@@ -782,13 +788,17 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
 
 int prcg_time_sweeps(prcg_ctx* c, int variant, int reps, float* ms_per_sweep, int* nsweeps) {
   if (!c || !ms_per_sweep || !nsweeps || reps < 1) return set_err(c, PRCG_ERR_INVALID, "bad argument");
-  if (variant < 0 || variant > 4) return set_err(c, PRCG_ERR_UNSUPPORTED, "variant not built");
+  if (variant < 0 || variant > 6) return set_err(c, PRCG_ERR_UNSUPPORTED, "variant not built");
   int phases[3];
   int np = 0;
   if (variant == V_HS) {
     phases[0] = PH_HS_A; phases[1] = PH_HS_B; phases[2] = PH_HS_C; np = 3;
   } else if (variant == V_PR || variant == V_M) {
     phases[0] = PH_PR_A; phases[1] = PH_PR_B; np = 2;
+  } else if (variant == V_CGCG) {
+    phases[0] = PH_CG_A; phases[1] = PH_CG_B; np = 2;
+  } else if (variant == V_GV) {
+    phases[0] = PH_GV; np = 1;
   } else {
     phases[0] = PH_PIPE; np = 1;
   }

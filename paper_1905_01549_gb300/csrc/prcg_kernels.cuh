@@ -72,7 +72,8 @@ template <class Op, class Pc>
 __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevState* S,
                                                    double* partials, int variant) {
   if (__ldcg(&S->done)) return;
-  const bool pipe = variant == V_PIPE || variant == V_PIPE_M;
+  const bool pipe = variant == V_PIPE || variant == V_PIPE_M || variant == V_GV;
+  const bool keep_w = variant == V_CGCG || variant == V_GV;
   double acc[3] = {0.0, 0.0, 0.0};
   const double* __restrict__ p = V.p[0];
   PRCG_ROWS(i, op.n) {
@@ -80,6 +81,8 @@ __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevStat
     const double st = Pc::on ? pc(i) * s : s;
     V.s[0][i] = s;
     if (Pc::on && pipe) V.st[0][i] = st;
+    if (keep_w) V.w[0][i] = s;   // w_0 = A r~_0 is the same product (p_0 = r~_0)
+    if (variant == V_GV) V.u[0][i] = 0.0;   // multiplied by beta_0 = 0 in the first sweep
     const double pi = __ldg(p + i);
     const double rt = Pc::on ? __ldg(V.rt[0] + i) : __ldg(V.r[0] + i);
     acc[0] += pi * s;
@@ -99,6 +102,9 @@ __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevStat
         breakdown(S);
       } else {
         S->alpha = nu / mu;
+        // CG-CG / GV-CG: the first sweep "updates" p_0, s_0 (, s~_0, u_0)
+        // with beta_0 = 0, which leaves the initial vectors as they are
+        S->beta = 0.0;
       }
     }
   }
@@ -329,6 +335,125 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
     S->rho = tot[4];
     if (!record_and_test(S, k, tot[4])) scalar_step_pr(S, meurant != 0);
   }
+}
+
+// ------------------------------------------------------- CG-CG (Appendix E)
+// Scalars of the Chronopoulos-Gear / Ghysels-Vanroose recurrences, formed by
+// the last CTA after the reduction of nu_k, eta_k, <r_k, r_k> (the order of
+// Appendix E: stopping test, beta_k, mu_k = eta_k - (beta_k / alpha_{k-1}) nu_k,
+// alpha_k).
+__device__ __forceinline__ void scalar_step_cg(DevState* S, int k, double nu, double eta,
+                                               double rho) {
+  S->rho = rho;
+  S->eta = eta;
+  if (record_and_test(S, k, rho)) return;
+  if (!finite(nu) || !(nu > 0.0)) { breakdown(S); return; }
+  const double beta = nu / S->nu;
+  const double mu = eta - (beta / S->alpha) * nu;
+  if (!finite(mu) || !(mu > 0.0)) { breakdown(S); return; }
+  S->beta = beta;
+  S->mu = mu;
+  S->nu = nu;
+  S->alpha = nu / mu;
+}
+
+// Sweep A of CG-CG iteration k: finish iteration k-1 (p_{k-1} = r~_{k-1} +
+// beta p, s_{k-1} = w_{k-1} + beta s), then x_k, r_k and r~_k = M^{-1} r_k.
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_cg_a(Op op, Pc pc, Vecs V, DevState* S) {
+  if (__ldcg(&S->done)) return;
+  const double alpha = __ldcg(&S->alpha);
+  const double beta = __ldcg(&S->beta);
+  double* __restrict__ x = V.x;
+  double* __restrict__ r = V.r[0];
+  double* __restrict__ rt = Pc::on ? V.rt[0] : V.r[0];
+  double* __restrict__ p = V.p[0];
+  double* __restrict__ s = V.s[0];
+  const double* __restrict__ w = V.w[0];
+  PRCG_ROWS(i, op.n) {
+    const double pn = fma(beta, p[i], rt[i]);
+    const double sn = fma(beta, s[i], __ldg(w + i));
+    p[i] = pn;
+    s[i] = sn;
+    x[i] = fma(alpha, pn, x[i]);
+    const double rn = fma(-alpha, sn, r[i]);
+    r[i] = rn;
+    if (Pc::on) V.rt[0][i] = pc(i) * rn;
+  }
+}
+
+// Sweep B of CG-CG iteration k: w_k = A r~_k, nu_k, eta_k = <r~_k, w_k>, <r_k, r_k>.
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_cg_b(Op op, Pc pc, Vecs V, DevState* S,
+                                                 double* partials) {
+  if (__ldcg(&S->done)) return;
+  const double* __restrict__ rt = Pc::on ? V.rt[0] : V.r[0];
+  const double* __restrict__ r = V.r[0];
+  double acc[3] = {0.0, 0.0, 0.0};
+  PRCG_ROWS(i, op.n) {
+    const double wn = op.row(i, [&](int j) { return __ldg(rt + j); });
+    V.w[0][i] = wn;
+    const double rti = __ldg(rt + i), ri = __ldg(r + i);
+    acc[0] = fma(rti, ri, acc[0]);
+    acc[1] = fma(rti, wn, acc[1]);
+    acc[2] = fma(ri, ri, acc[2]);
+  }
+  double tot[3];
+  if (grid_sum<3>(acc, partials, S, tot) && threadIdx.x == 0)
+    scalar_step_cg(S, S->k + 1, Pc::on ? tot[0] : tot[2], tot[1], tot[2]);
+}
+
+// --------------------------------------------------- GV-CG (Appendix E)
+// One sweep per iteration k: t_{k-1} = A M^{-1} w_{k-1} from the stored
+// w_{k-1} (buffer qr), the updates that finish iteration k-1 (p, s, s~,
+// u with beta_{k-1}), the updates of iteration k (x_k, r_k, r~_k by
+// recurrence, w_k = w_{k-1} - alpha u_{k-1}, to buffer qw) and nu_k, eta_k.
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_gv(Op op, Pc pc, Vecs V, DevState* S,
+                                               double* partials, int qr, int qw) {
+  if (__ldcg(&S->done)) return;
+  const double alpha = __ldcg(&S->alpha);
+  const double beta = __ldcg(&S->beta);
+  const double* __restrict__ w_o = V.w[qr];
+  double* __restrict__ x = V.x;
+  double* __restrict__ r = V.r[0];
+  double* __restrict__ p = V.p[0];
+  double* __restrict__ s = V.s[0];
+  double* __restrict__ u = V.u[0];
+  double acc[3] = {0.0, 0.0, 0.0};
+  PRCG_ROWS(i, op.n) {
+    const double t = op.row(i, [&](int j) {
+      const double wj = __ldg(w_o + j);
+      return Pc::on ? pc(j) * wj : wj;
+    });
+    const double wi = __ldg(w_o + i);
+    const double rti = Pc::on ? V.rt[0][i] : r[i];
+    const double pn = fma(beta, p[i], rti);
+    const double sn = fma(beta, s[i], wi);
+    const double un = fma(beta, u[i], t);
+    double stn = sn;
+    if (Pc::on) stn = fma(beta, V.st[0][i], pc(i) * wi);
+    p[i] = pn;
+    s[i] = sn;
+    u[i] = un;
+    x[i] = fma(alpha, pn, x[i]);
+    const double rn = fma(-alpha, sn, r[i]);
+    r[i] = rn;
+    double rtn = rn;
+    if (Pc::on) {
+      V.st[0][i] = stn;
+      rtn = fma(-alpha, stn, rti);
+      V.rt[0][i] = rtn;
+    }
+    const double wn = fma(-alpha, un, wi);
+    V.w[qw][i] = wn;
+    acc[0] = fma(rtn, rn, acc[0]);
+    acc[1] = fma(rtn, wn, acc[1]);
+    acc[2] = fma(rn, rn, acc[2]);
+  }
+  double tot[3];
+  if (grid_sum<3>(acc, partials, S, tot) && threadIdx.x == 0)
+    scalar_step_cg(S, S->k + 1, Pc::on ? tot[0] : tot[2], tot[1], tot[2]);
 }
 
 // ------------------------------------------------ mixed precision (FP32 inner)

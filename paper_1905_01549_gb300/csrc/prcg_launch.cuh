@@ -22,7 +22,10 @@ enum Phase {
   PH_MX_INIT_B = 11,
   PH_MX_PR_A = 12,
   PH_MX_PR_B = 13,
-  PH_MX_UPDATE = 14
+  PH_MX_UPDATE = 14,
+  PH_CG_A = 15,
+  PH_CG_B = 16,
+  PH_GV = 17
 };
 
 struct Plan {
@@ -178,6 +181,21 @@ cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, 
       }
       auto k = k_pipe<Op, Pc>;
       k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw, meurant);
+      break;
+    }
+    case PH_CG_A: {
+      auto k = k_cg_a<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S);
+      break;
+    }
+    case PH_CG_B: {
+      auto k = k_cg_b<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);
+      break;
+    }
+    case PH_GV: {
+      auto k = k_gv<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw);
       break;
     }
     case PH_TRUE_RES: {

@@ -26,7 +26,7 @@ def case(name):
 
 
 CASES = ["poisson2d_64", "poisson3d_ragged", "varcoef3d_ragged", "varcoef2d_ragged", "shifted2d"]
-GPU_VARIANTS = ["hs", "pr", "pipe_pr", "m", "pipe_m"]
+GPU_VARIANTS = ["hs", "pr", "pipe_pr", "m", "pipe_m", "cgcg", "gv"]
 
 
 def make_solver(G, prob, op, precond):
