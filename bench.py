@@ -266,6 +266,19 @@ def time_solves(S, b, variant, tol, maxit, steps, warmup):
                 loop_ms=res.loop_ms, status=res.status)
 
 
+def aggregate_ranks(dev_s: float, iters: int, dist=None, device: str = "cuda"):
+    """Whole-job numbers of a replica run: the slowest rank's time (max) and
+    the iterations of all ranks (sum).  Single process: the inputs."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(dev_s), float(iters)
+    import torch
+    t = torch.tensor([float(dev_s)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    it = torch.tensor([float(iters)], dtype=torch.float64, device=device)
+    dist.all_reduce(it, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(it.item())
+
+
 def run_ours(args):
     import torch
     import paper_1905_01549_gb300 as G
@@ -296,14 +309,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     dev_s = sum(main["dev_ms"]) / 1e3
     tot_iters = sum(main["iters"])
-    if dist is not None:
-        t = torch.tensor([dev_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        it = torch.tensor([float(tot_iters)], device="cuda")
-        dist.all_reduce(it, op=dist.ReduceOp.SUM)
-        dev_s_max, all_iters = float(t.item()), float(it.item())
-    else:
-        dev_s_max, all_iters = dev_s, float(tot_iters)
+    dev_s_max, all_iters = aggregate_ranks(dev_s, tot_iters, dist, "cuda")
     value = all_iters / dev_s_max
     K = main["iters"][-1]
     clocks = clk.summary()
