@@ -121,6 +121,10 @@ int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t
  * Returns PRCG_OK, PRCG_NOT_CONVERGED, PRCG_BREAKDOWN (x holds x_K in all
  * three) or a negative error (x untouched).  If b == 0, x is set to 0 and
  * K = 0.  The call blocks until the result is on the host.
+ * Execution: for n <= 2^21 (environment PRCG_PERSIST_MAX overrides) HS, PR,
+ * M, pipe-PR and pipe-M run as one persistent cooperative kernel (grid
+ * barriers instead of kernel boundaries); larger systems, CG-CG and GV run
+ * as one CUDA graph launch with a device-side while loop.
  */
 int prcg_solve(prcg_ctx* ctx, int variant, const double* b, double* x,
                double tol, int maxit, double* residual_history,

@@ -245,6 +245,8 @@ struct prcg_ctx {
   float* pool32 = nullptr;       // FP32 vectors of the mixed-precision inner solve
   float* sval32 = nullptr;       // FP32 copy of the SELL values
   DevState* S2 = nullptr;        // scalar block of the inner solve
+  GridBar* gb = nullptr;         // grid barrier of the persistent solve
+  int persist_max = 1 << 21;     // largest n solved by the persistent kernel
   std::string err;
 };
 
@@ -309,7 +311,10 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   }
   c->plan.pc.d = d;
   if (taken != nv) return set_err(c, PRCG_ERR_INVALID, "internal: vector pool size mismatch");
-  CK(cudaMalloc(&c->partials, (size_t)kMaxGrid * (kMaxNV + 2) * sizeof(double)));
+  // partial sums: kMaxGrid x (kMaxNV + 2) for the sweeps, and two epochs of
+  // kMaxPersistCtas x 8 for the persistent solve's barriers (the larger)
+  CK(cudaMalloc(&c->partials, std::max((size_t)kMaxGrid * (kMaxNV + 2), (size_t)2 * kMaxPersistCtas * 8) *
+                                  sizeof(double)));
   CK(cudaMalloc(&c->S, sizeof(DevState)));
   CK(cudaMemset(c->S, 0, sizeof(DevState)));
   CK(cudaMallocHost(&c->hS, sizeof(DevState)));
@@ -318,8 +323,12 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   c->plan.S = c->S;
   c->plan.partials = c->partials;
   c->plan.partials_a = c->partials + (size_t)kMaxGrid * kMaxNV;
+  CK(cudaMalloc(&c->gb, sizeof(GridBar)));
+  c->plan.gb = c->gb;
   const char* ng = getenv("PRCG_NO_GRAPH");
   c->use_graph = !(ng && ng[0] == '1');
+  const char* pm = getenv("PRCG_PERSIST_MAX");
+  if (pm) c->persist_max = atoi(pm);
   return PRCG_OK;
 }
 
@@ -718,7 +727,11 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
     CK(cudaMalloc(&c->hist, (size_t)(maxit + 1) * sizeof(double)));
     c->hist_cap = maxit + 1;
   }
-  bool graph = c->use_graph;
+  // small and medium systems: the whole solve as one persistent cooperative launch
+  const bool persist = n <= c->persist_max &&
+                       (variant == V_HS || variant == V_PR || variant == V_M || variant == V_PIPE ||
+                        variant == V_PIPE_M);
+  bool graph = !persist && c->use_graph;
   if (graph && build_graph(c, variant) != PRCG_OK) graph = false;  // fall back to the host loop
   const int chunk = graph ? c->graphs[variant].chunk : chunk_for(c);
   if ((rc = wait_user(c)) != PRCG_OK) return rc;
@@ -727,17 +740,33 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   DevState& h = *c->hS;
   memset(&h, 0, sizeof h);
   h.tol = tol;
+  h.tol2 = tol * tol;
   h.hist = c->hist;
   h.maxit = maxit;
   h.maxbodies = maxit / chunk + 3;
   h.status = kRunning;
   CK(cudaMemcpyAsync(c->S, &h, sizeof h, cudaMemcpyHostToDevice, c->cs));
   CK(cudaEventRecord(c->ev_start, c->cs));
-  if (graph) {
-    CK(cudaGraphLaunch(c->graphs[variant].exec, c->cs));
-  } else {
-    c->host_loop_launches = 0;
-    if ((rc = run_host_loop(c, variant, maxit)) != PRCG_OK) return rc;
+  bool persisted = false;
+  if (persist) {
+    CK(cudaMemsetAsync(c->gb, 0, sizeof(GridBar), c->cs));
+    CK(cudaEventRecord(c->ev_init, c->cs));
+    cudaError_t e = c->launch(c->plan, PH_PERSIST, variant, 0, 0, c->cs);
+    if (e == cudaSuccess) {
+      persisted = true;
+      CK(cudaEventRecord(c->ev_loop, c->cs));
+    } else {
+      cudaGetLastError();   // not launchable cooperatively here: use the graph path
+      graph = c->use_graph && build_graph(c, variant) == PRCG_OK;
+    }
+  }
+  if (!persisted) {
+    if (graph) {
+      CK(cudaGraphLaunch(c->graphs[variant].exec, c->cs));
+    } else {
+      c->host_loop_launches = 0;
+      if ((rc = run_host_loop(c, variant, maxit)) != PRCG_OK) return rc;
+    }
   }
   CK(cudaMemcpyAsync(&h, c->S, sizeof h, cudaMemcpyDeviceToHost, c->cs));
   CK(cudaStreamSynchronize(c->cs));
@@ -745,7 +774,9 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   {
     const int64_t per_iter = iter_launches(variant);
     int64_t launches = init_launches(variant);
-    if (graph)
+    if (persisted)
+      launches = 1;
+    else if (graph)
       launches += (int64_t)h.bodies * (chunk * per_iter + 1);
     else
       launches += c->host_loop_launches;
@@ -757,9 +788,18 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   if (status < 0) return set_err(c, status, "device loop exceeded its iteration limit");
   if (h.zero_rhs) CK(cudaMemsetAsync(c->plan.v.x, 0, (size_t)n * sizeof(double), c->cs));
   CK(cudaMemcpyAsync(x, c->plan.v.x, (size_t)n * sizeof(double), cudaMemcpyDefault, c->cs));
-  if (residual_history)
-    CK(cudaMemcpyAsync(residual_history, c->hist, (size_t)(K + 1) * sizeof(double),
+  if (residual_history) {
+    // the device recorded rho_k = ||r_k||^2: convert to ||r_k|| / ||b||
+    std::vector<double> hh(K + 1);
+    CK(cudaMemcpyAsync(hh.data(), c->hist, (size_t)(K + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                       c->cs));
+    CK(cudaStreamSynchronize(c->cs));
+    const double bn = sqrt(h.bnorm2);
+    for (int k = 0; k <= K; ++k) hh[k] = bn > 0.0 ? sqrt(hh[k]) / bn : 0.0;
+    CK(cudaMemcpyAsync(residual_history, hh.data(), (size_t)(K + 1) * sizeof(double),
                        cudaMemcpyDefault, c->cs));
+    CK(cudaStreamSynchronize(c->cs));
+  }
   if (final_true_relres_out) {
     if (h.zero_rhs) {
       *final_true_relres_out = 0.0;
@@ -906,6 +946,7 @@ int prcg_solve_f32_refined(prcg_ctx* c, const double* b, double* x, double tol, 
     DevState& hs = *c->hS;
     memset(&hs, 0, sizeof hs);
     hs.tol = std::max(inner_tol, std::min(0.5, 0.25 * tol / rel));
+    hs.tol2 = hs.tol * hs.tol;
     hs.maxit = inner_maxit;
     hs.status = kRunning;
     hs.arg = 1.0 / tn;
@@ -1057,6 +1098,7 @@ int prcg_destroy(prcg_ctx* c) {
   if (c->pool32) cudaFree(c->pool32);
   if (c->sval32) cudaFree(c->sval32);
   if (c->S2) cudaFree(c->S2);
+  if (c->gb) cudaFree(c->gb);
   if (c->sell_v) cudaFree(c->sell_v);
   if (c->partials) cudaFree(c->partials);
   if (c->S) cudaFree(c->S);

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/prcg.h"
+#include "prcg_reduce.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -37,49 +38,40 @@ struct BatchSys {
 
 constexpr int kMaxThreads = 1024;
 
-template <int NV>
-__device__ __forceinline__ void cta_sum(double (&v)[NV], double* sm) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nw = blockDim.x >> 5;
-#pragma unroll
-  for (int m = 0; m < NV; ++m)
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[m] += __shfl_down_sync(0xffffffffu, v[m], o);
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int m = 0; m < NV; ++m) sm[m * 32 + wid] = v[m];
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int m = 0; m < NV; ++m) {
-      double t = lane < nw ? sm[m * 32 + lane] : 0.0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      v[m] = t;
-    }
-  }
-}
-
-// Cluster-wide sum: CTA totals go to a double-buffered shared slot, one
-// cluster barrier, then every thread adds all ranks' slots in rank order.
-template <int NV>
+// Cluster-wide sum followed by the scalar step.  CTA totals go to a
+// double-buffered shared slot and, after one cluster barrier, warp 0 of every
+// CTA gathers the ranks' slots (lane r takes rank r) and adds them in a fixed
+// tree, so all CTAs of the cluster form bitwise-identical totals.  Warp 0
+// alone then runs `step(tot, bc)`, which leaves its results in the shared
+// array bc (lane 0 stores): the FP64 pipe issues two lanes per clock per SM
+// here, so neither the rank sums nor the divisions of the scalar step are
+// repeated in every warp.  Ranks are at most 32 (portable clusters are <= 8,
+// non-portable <= 16).
+template <int NV, class Step>
 __device__ __forceinline__ void cluster_sum(double (&v)[NV], double* sm, double* slots, int& parity,
-                                            cg::cluster_group& cl, double (&tot)[NV]) {
-  cta_sum<NV>(v, sm);
+                                            cg::cluster_group& cl, bool warp_active, Step&& step) {
+  prcg::block_sum<NV>(v, sm, warp_active);
   double* mine = slots + parity * 8;
   if (threadIdx.x == 0)
 #pragma unroll
     for (int m = 0; m < NV; ++m) mine[m] = v[m];
   cl.sync();
+  if (threadIdx.x < 32) {
+    const unsigned lane = threadIdx.x;
+    double t[NV];
+    const bool has = lane < cl.num_blocks();
+    const double* rs = cl.map_shared_rank(mine, has ? lane : 0u);
 #pragma unroll
-  for (int m = 0; m < NV; ++m) tot[m] = 0.0;
-  const unsigned nb = cl.num_blocks();
-  for (unsigned r = 0; r < nb; ++r) {
-    const double* rs = cl.map_shared_rank(mine, r);
+    for (int m = 0; m < NV; ++m) t[m] = has ? rs[m] : 0.0;
+    __syncwarp();
+    prcg::warp_sum_store<NV>(t, sm, 1);   // totals to sm[0..NV)
+    __syncwarp();
+    double tot[NV];
 #pragma unroll
-    for (int m = 0; m < NV; ++m) tot[m] += rs[m];
+    for (int m = 0; m < NV; ++m) tot[m] = sm[m];
+    step(tot);
   }
+  __syncthreads();
   parity ^= 1;
 }
 
@@ -119,6 +111,8 @@ __global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
   const int g0 = (int)(crank * blockDim.x + threadIdx.x);
   __shared__ double sm[5 * 32];
   __shared__ double slots[2 * 8];
+  __shared__ double bc[3];      // what warp 0 decided, read by every thread
+  __shared__ int bst;           // status decided by warp 0 (-100: running)
   __shared__ int s_next;
   int parity = 0;
   for (;;) {
@@ -130,6 +124,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
     const int id = a.order[qi];
     const BatchSys q = a.sys[id];
     const int n = q.nx * q.ny;
+    const bool wact = g0 - (int)(threadIdx.x & 31) < n;   // this warp owns rows
     const double* b = a.b + q.off;
     double* x = a.x + q.off;
     double* r = a.r + q.off;
@@ -150,22 +145,28 @@ __global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
       i3[1] = fma(ri, ri, i3[1]);
       i3[2] = fma(bi, bi, i3[2]);
     }
-    double t3[3];
-    cluster_sum<3>(i3, sm, slots, parity, cl, t3);
-    double nu = t3[0];
-    const double bnorm = sqrt(t3[2]);
-    int status = -100, K = 0;
-    if (t3[2] == 0.0) {
-      status = 0;
+    // bc = {nu_0, tol^2 ||b||^2 (||r||^2 <= that stops), b == 0, status}
+    cluster_sum<3>(i3, sm, slots, parity, cl, wact, [&](const double* t) {
+      const double stop2 = a.tol * a.tol * t[2];
+      int st = -100;
+      if (t[2] == 0.0 || t[1] <= stop2)
+        st = 0;
+      else if (a.maxit == 0)
+        st = 1;
+      if (threadIdx.x == 0) {
+        bc[0] = t[0];
+        bc[1] = stop2;
+        bc[2] = t[2] == 0.0 ? 1.0 : 0.0;
+        bst = st;
+      }
+    });
+    double nu = bc[0];
+    const double stop2 = bc[1];
+    int status = bst, K = 0;
+    if (bc[2] != 0.0)
       for (int i = g0; i < n; i += G) x[i] = 0.0;
-    } else if (sqrt(t3[1]) / bnorm <= a.tol) {
-      status = 0;
-    } else if (a.maxit == 0) {
-      status = 1;
-    }
-    double alpha = 0.0, beta = 0.0;
     if (status == -100) {
-      // s_0 = A p_0; mu_0, sigma_0, gamma_0
+      // s_0 = A p_0; mu_0, sigma_0, gamma_0 -> alpha_1, beta_1 (Eq. 2.3)
       double j3[3] = {0.0, 0.0, 0.0};
       for (int i = g0; i < n; i += G) {
         const double si = stencil_row(q, p, i);
@@ -174,20 +175,26 @@ __global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
         j3[1] = fma(rt[i], si, j3[1]);
         j3[2] = fma(si, si, j3[2]);
       }
-      double u3[3];
-      cluster_sum<3>(j3, sm, slots, parity, cl, u3);
-      double mu = u3[0], sigma = u3[1], gamma = a.jacobi ? d * u3[2] : u3[2];
-      for (int k = 1; k <= a.maxit; ++k) {
-        // scalar step (identical in every thread of the cluster)
-        alpha = nu / mu;
-        const double nu_pred = nu - 2.0 * alpha * sigma + alpha * alpha * gamma;
-        if (!isfinite(nu) || !isfinite(mu) || !(mu > 0.0) || nu < 0.0 || !isfinite(nu_pred) ||
-            nu_pred < 0.0 || nu == 0.0) {
-          status = 2;
-          K = k - 1;
-          break;
+      // the scalar step: alpha_k = nu/mu, nu'_{k+1} = nu - 2 alpha sigma + alpha^2 gamma,
+      // beta = nu'/nu; status 2 on breakdown
+      auto scalars = [&](double nu_, double mu, double sigma, double gamma) {
+        const double alpha = nu_ / mu;
+        const double nu_pred = nu_ - 2.0 * alpha * sigma + alpha * alpha * gamma;
+        const bool bad = !isfinite(nu_) || !isfinite(mu) || !(mu > 0.0) || nu_ < 0.0 ||
+                         !isfinite(nu_pred) || nu_pred < 0.0 || nu_ == 0.0;
+        if (threadIdx.x == 0) {
+          bc[0] = alpha;
+          bc[1] = bad ? 0.0 : nu_pred / nu_;
+          bc[2] = nu_;
+          bst = bad ? 2 : -100;
         }
-        beta = nu_pred / nu;
+      };
+      cluster_sum<3>(j3, sm, slots, parity, cl, wact, [&](const double* t) {
+        scalars(nu, t[0], t[1], a.jacobi ? d * t[2] : t[2]);
+      });
+      status = bst;
+      double alpha = bc[0], beta = bc[1];
+      for (int k = 1; status == -100 && k <= a.maxit; ++k) {
         // sweep A: x_k, r_k, r~_k, p_k
         double a2[2] = {0.0, 0.0};
         for (int i = g0; i < n; i += G) {
@@ -216,18 +223,18 @@ __global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
           a5[3] = fma(rtv[i], sn, a5[3]);
           a5[4] = fma(sn, sn, a5[4]);
         }
-        double t5[5];
-        cluster_sum<5>(a5, sm, slots, parity, cl, t5);
-        nu = t5[0];
-        mu = t5[2];
-        sigma = t5[3];
-        gamma = a.jacobi ? d * t5[4] : t5[4];
+        // stop on ||r_k||^2 <= tol^2 ||b||^2, else the scalars of iteration k + 1
+        cluster_sum<5>(a5, sm, slots, parity, cl, wact, [&](const double* t) {
+          if (t[1] <= stop2 || k == a.maxit) {
+            if (threadIdx.x == 0) bst = t[1] <= stop2 ? 0 : 1;
+          } else {
+            scalars(t[0], t[2], t[3], a.jacobi ? d * t[4] : t[4]);
+          }
+        });
         K = k;
-        if (sqrt(t5[1]) / bnorm <= a.tol) {
-          status = 0;
-          break;
-        }
-        if (k == a.maxit) status = 1;
+        status = bst;
+        alpha = bc[0];
+        beta = bc[1];
       }
     }
     if (crank == 0 && threadIdx.x == 0) {
@@ -250,7 +257,7 @@ __global__ void k_batched_true_res(BatchArgs a, double* out) {
       v[0] = fma(t, t, v[0]);
       v[1] = fma(bi, bi, v[1]);
     }
-    cta_sum<2>(v, sm);
+    prcg::block_sum<2>(v, sm);
     if (threadIdx.x == 0) out[id] = v[1] > 0.0 ? sqrt(v[0]) / sqrt(v[1]) : 0.0;
     __syncthreads();
   }

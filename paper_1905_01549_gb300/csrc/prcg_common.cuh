@@ -9,6 +9,8 @@
 
 #include <type_traits>
 
+#include "prcg_reduce.cuh"
+
 namespace prcg {
 
 constexpr int kBlock = 256;             // threads per CTA for every sweep
@@ -28,6 +30,7 @@ struct DevState {
   double bnorm2;
   // per-solve parameters
   double tol;
+  double tol2;           // tol^2: the stopping test compares squared norms
   double* hist;          // device array, >= maxit + 1 entries
   int maxit;
   int maxbodies;         // safety limit for the device-side while loop
@@ -83,33 +86,6 @@ struct KahanF {
 __device__ __forceinline__ double ldcs(const double* p) { return __ldcs(p); }
 __device__ __forceinline__ double ldg(const double* p) { return __ldg(p); }
 
-// Sum v[0..NV) over the CTA in a fixed order; the result is valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double* sm) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nwarps = (blockDim.x + 31) >> 5;
-#pragma unroll
-  for (int m = 0; m < NV; ++m) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[m] += __shfl_down_sync(0xffffffffu, v[m], off);
-  }
-  __syncthreads();  // sm may still be read by a previous call
-  if (lane == 0) {
-#pragma unroll
-    for (int m = 0; m < NV; ++m) sm[m * 32 + wid] = v[m];
-  }
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int m = 0; m < NV; ++m) {
-      double t = lane < nwarps ? sm[m * 32 + lane] : 0.0;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-      v[m] = t;
-    }
-  }
-}
-
 // Grid-wide sum of v: each CTA writes its partial, the last CTA to arrive
 // adds all partials in CTA order (deterministic for a fixed grid) and
 // returns true with the totals in tot (thread 0).  No CTA ever waits.
@@ -136,7 +112,7 @@ __device__ __forceinline__ bool grid_sum(double (&v)[NV], double* partials, DevS
 #pragma unroll
     for (int m = 0; m < NV; ++m) acc[m] += __ldcg(&partials[b * NV + m]);
   }
-  block_sum<NV>(acc, sm);
+  block_sum<NV>(acc, sm, (threadIdx.x & ~31) < (int)gridDim.x);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int m = 0; m < NV; ++m) tot[m] = acc[m];
@@ -152,13 +128,14 @@ __device__ __forceinline__ bool finite(double v) { return isfinite(v); }
 // --------------------------------------------------------------------------
 
 // Decide convergence for iteration k from rho_k = <r_k, r_k>; returns true
-// (and finishes the run) when ||r_k|| / ||b|| <= tol or k == maxit.
+// (and finishes the run) when ||r_k||^2 <= tol^2 ||b||^2 or k == maxit.
+// The history records rho_k; the host converts it to ||r_k|| / ||b|| (a
+// square root and a division cost ~1000 cycles of FP64 latency here).
 __device__ __forceinline__ bool record_and_test(DevState* S, int k, double rho) {
   S->k = k;
   if (S->profile) return false;
-  const double rel = sqrt(rho) / sqrt(S->bnorm2);
-  if (S->hist) S->hist[k] = rel;
-  if (rel <= S->tol) {
+  if (S->hist) S->hist[k] = rho;
+  if (rho <= S->tol2 * S->bnorm2) {
     S->status = 0;
     S->done = 1;
     return true;

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_b(Op op, Pc pc, Vecs V, DevState*
     a2[1] += __ldcg(&partials_a[b * 2 + 1]);
   }
   __shared__ double sm2[2 * 32];
-  block_sum<2>(a2, sm2);
+  block_sum<2>(a2, sm2, (threadIdx.x & ~31) < grid_a);
   if (threadIdx.x == 0) {
     double nu = a2[0], rho = a2[1];
     if (!Pc::on) nu = rho;
@@ -595,7 +595,7 @@ __global__ void __launch_bounds__(kBlock) k_mx_pr_b(Op op, Pc pc, Vecs32 W, DevS
     a2[1] += __ldcg(&partials_a[b * 2 + 1]);
   }
   __shared__ double sm2[2 * 32];
-  block_sum<2>(a2, sm2);
+  block_sum<2>(a2, sm2, (threadIdx.x & ~31) < grid_a);
   if (threadIdx.x == 0) {
     const int k = S->k + 1;
     S->mu = tot[0];

@@ -3,6 +3,7 @@
 // library compiles in parallel translation units.
 #pragma once
 
+#include "prcg_persistent.cuh"
 #include "prcg_tma.cuh"
 
 namespace prcg {
@@ -25,7 +26,8 @@ enum Phase {
   PH_MX_UPDATE = 14,
   PH_CG_A = 15,
   PH_CG_B = 16,
-  PH_GV = 17
+  PH_GV = 17,
+  PH_PERSIST = 18   // the whole solve as one cooperative launch (HS, PR, M, pipe, pipe-M)
 };
 
 struct Plan {
@@ -41,7 +43,27 @@ struct Plan {
   Vecs32 w;
   DevState* S2;
   double arg;
+  GridBar* gb;   // grid barrier of the persistent solve
 };
+
+// Cooperative launch of the persistent solve: one CTA per SM.
+template <class Op, class Pc, int VARIANT>
+cudaError_t launch_persist(const Plan& P, int meurant, cudaStream_t st) {
+  auto k = k_persist<Op, Pc, VARIANT>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kPersistThreads, 0);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1 || P.sms > kMaxPersistCtas) return cudaErrorCooperativeLaunchTooLarge;
+  Op op(P.op);
+  Pc pc(P.pc);
+  Vecs v = P.v;
+  DevState* S = P.S;
+  double* partials = P.partials;
+  GridBar* gb = P.gb;
+  void* args[] = {(void*)&op, (void*)&pc, (void*)&v, (void*)&S, (void*)&partials, (void*)&gb,
+                  (void*)&meurant};
+  return cudaLaunchCooperativeKernel((const void*)k, dim3(P.sms), dim3(kPersistThreads), args, 0, st);
+}
 
 using LaunchFn = cudaError_t (*)(const Plan&, int phase, int variant, int qr, int qw,
                                  cudaStream_t);
@@ -198,6 +220,11 @@ cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, 
       k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw);
       break;
     }
+    case PH_PERSIST:
+      if (variant == V_HS) return launch_persist<Op, Pc, V_HS>(P, 0, st);
+      if (variant == V_PR || variant == V_M) return launch_persist<Op, Pc, V_PR>(P, meurant, st);
+      if (variant == V_PIPE || variant == V_PIPE_M) return launch_persist<Op, Pc, V_PIPE>(P, meurant, st);
+      return cudaErrorInvalidValue;
     case PH_TRUE_RES: {
       auto k = k_true_res<Op, Pc>;
       k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);

@@ -22,6 +22,7 @@
 #include <cmath>
 
 #include "../../include/prcg.h"
+#include "prcg_reduce.cuh"
 
 namespace {
 
@@ -64,29 +65,6 @@ __device__ __forceinline__ double apply_row(const NoallocArgs& a, int i, const d
   return acc;
 }
 
-template <int NV>
-__device__ __forceinline__ void cta_sum(double (&v)[NV], double* sm) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int m = 0; m < NV; ++m)
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v[m] += __shfl_down_sync(0xffffffffu, v[m], off);
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int m = 0; m < NV; ++m) sm[m * 32 + wid] = v[m];
-  __syncthreads();
-  if (wid == 0) {
-#pragma unroll
-    for (int m = 0; m < NV; ++m) {
-      double t = sm[m * 32 + lane];
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-      v[m] = t;
-    }
-  }
-}
-
 // The whole PR-CG run (initialize(), then Algorithm 2 with the scalars
 // formed at the start of each iteration) in one CTA.  Vectors live in the
 // scratch array; they are written and read by different threads of this CTA
@@ -119,7 +97,7 @@ k_pr_noalloc(NoallocArgs a, double* scratch) {
     acc3[1] += ri * ri;
     acc3[2] += a.b[i] * a.b[i];
   }
-  cta_sum<3>(acc3, sm);
+  prcg::block_sum<3>(acc3, sm);
   __shared__ double st_nu, st_bn2;
   if (tid == 0) {
     st_nu = acc3[0];
@@ -147,7 +125,7 @@ k_pr_noalloc(NoallocArgs a, double* scratch) {
       acc[2] += sti * si;
     }
   }
-  cta_sum<5>(acc, sm);
+  prcg::block_sum<5>(acc, sm);
   double nu = 0.0, mu = 0.0, sigma = 0.0, gamma = 0.0;
   if (tid == 0) {
     nu = st_nu;
@@ -215,7 +193,7 @@ k_pr_noalloc(NoallocArgs a, double* scratch) {
       a5[3] += rtn * rn;
       a5[4] += rn * rn;
     }
-    cta_sum<5>(a5, sm);
+    prcg::block_sum<5>(a5, sm);
     if (tid == 0) {
       mu = a5[0];
       sigma = a5[1];

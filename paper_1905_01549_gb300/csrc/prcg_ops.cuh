@@ -117,21 +117,37 @@ struct SellOp {
       if (t < L) f(j[t], a[t]);
     for (int t = 8; t < L; ++t) f(__ldg(scol + base + 32 * t), __ldg(sval + base + 32 * t));
   }
+  // two interleaved accumulators halve the dependent FMA chain (an FP64 FMA
+  // has 64 cycles of latency on GB300)
   template <class G>
   __device__ __forceinline__ double row(int i, G&& g) const {
-    double acc = 0.0;
-    visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
-    return acc;
+    double a0 = 0.0, a1 = 0.0;
+    int t = 0;
+    visit(i, [&](int j, double a) {
+      if (t & 1)
+        a1 = fma(a, g(j), a1);
+      else
+        a0 = fma(a, g(j), a0);
+      ++t;
+    });
+    return a0 + a1;
   }
   template <class G1, class G2>
   __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
-    double c1 = 0.0, c2 = 0.0;
+    double c1 = 0.0, c2 = 0.0, e1 = 0.0, e2 = 0.0;
+    int t = 0;
     visit(i, [&](int j, double a) {
-      c1 = fma(a, g1(j), c1);
-      c2 = fma(a, g2(j), c2);
+      if (t & 1) {
+        e1 = fma(a, g1(j), e1);
+        e2 = fma(a, g2(j), e2);
+      } else {
+        c1 = fma(a, g1(j), c1);
+        c2 = fma(a, g2(j), c2);
+      }
+      ++t;
     });
-    a1 = c1;
-    a2 = c2;
+    a1 = c1 + e1;
+    a2 = c2 + e2;
   }
 };
 
@@ -161,11 +177,20 @@ struct StencilOp {
     f(y < ny - 1 ? i + nx : i, y < ny - 1 ? -1.0 : 0.0);
     if (DIM == 3) f(z < nz - 1 ? i + pl : i, z < nz - 1 ? -1.0 : 0.0);
   }
+  // two interleaved accumulators halve the dependent FMA chain (an FP64 FMA
+  // has 64 cycles of latency on GB300)
   template <class G>
   __device__ __forceinline__ double row(int i, G&& g) const {
-    double acc = 0.0;
-    visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
-    return acc;
+    double a0 = 0.0, a1 = 0.0;
+    int t = 0;
+    visit(i, [&](int j, double a) {
+      if (t & 1)
+        a1 = fma(a, g(j), a1);
+      else
+        a0 = fma(a, g(j), a0);
+      ++t;
+    });
+    return a0 + a1;
   }
   template <class G>
   __device__ __forceinline__ float row32(int i, G&& g) const {
@@ -175,13 +200,20 @@ struct StencilOp {
   }
   template <class G1, class G2>
   __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
-    double c1 = 0.0, c2 = 0.0;
+    double c1 = 0.0, c2 = 0.0, e1 = 0.0, e2 = 0.0;
+    int t = 0;
     visit(i, [&](int j, double a) {
-      c1 = fma(a, g1(j), c1);
-      c2 = fma(a, g2(j), c2);
+      if (t & 1) {
+        e1 = fma(a, g1(j), e1);
+        e2 = fma(a, g2(j), e2);
+      } else {
+        c1 = fma(a, g1(j), c1);
+        c2 = fma(a, g2(j), c2);
+      }
+      ++t;
     });
-    a1 = c1;
-    a2 = c2;
+    a1 = c1 + e1;
+    a2 = c2 + e2;
   }
 };
 
@@ -218,11 +250,20 @@ struct VarStencilOp {
     f(y < ny - 1 ? i + nx : i, y < ny - 1 ? -cyp : 0.0);
     if (DIM == 3) f(z < nz - 1 ? i + pl : i, z < nz - 1 ? -czp : 0.0);
   }
+  // two interleaved accumulators halve the dependent FMA chain (an FP64 FMA
+  // has 64 cycles of latency on GB300)
   template <class G>
   __device__ __forceinline__ double row(int i, G&& g) const {
-    double acc = 0.0;
-    visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
-    return acc;
+    double a0 = 0.0, a1 = 0.0;
+    int t = 0;
+    visit(i, [&](int j, double a) {
+      if (t & 1)
+        a1 = fma(a, g(j), a1);
+      else
+        a0 = fma(a, g(j), a0);
+      ++t;
+    });
+    return a0 + a1;
   }
   template <class G>
   __device__ __forceinline__ float row32(int i, G&& g) const {
@@ -232,13 +273,20 @@ struct VarStencilOp {
   }
   template <class G1, class G2>
   __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
-    double c1 = 0.0, c2 = 0.0;
+    double c1 = 0.0, c2 = 0.0, e1 = 0.0, e2 = 0.0;
+    int t = 0;
     visit(i, [&](int j, double a) {
-      c1 = fma(a, g1(j), c1);
-      c2 = fma(a, g2(j), c2);
+      if (t & 1) {
+        e1 = fma(a, g1(j), e1);
+        e2 = fma(a, g2(j), e2);
+      } else {
+        c1 = fma(a, g1(j), c1);
+        c2 = fma(a, g2(j), c2);
+      }
+      ++t;
     });
-    a1 = c1;
-    a2 = c2;
+    a1 = c1 + e1;
+    a2 = c2 + e2;
   }
 };
 

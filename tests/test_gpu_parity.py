@@ -233,3 +233,31 @@ def test_reruns_are_bitwise_identical(G, torch_mod):
             r2 = S.solve(b, variant=variant, tol=1e-10, maxit=5000, history=True)
             assert r1.iters == r2.iters
             assert torch.equal(r1.x, r2.x) and np.array_equal(r1.hist, r2.hist)
+
+
+@pytest.mark.parametrize("name,op,precond", [("poisson3d_ragged", "csr", "jacobi"),
+                                             ("varcoef2d_ragged", "csr", "jacobi"),
+                                             ("varcoef3d_ragged", "stencil", "jacobi"),
+                                             ("poisson2d_64", "stencil", "none")])
+def test_persistent_and_graph_paths_match_oracle(G, torch_mod, name, op, precond, monkeypatch):
+    """Small systems run as one persistent cooperative kernel by default; the
+    graph path (PRCG_PERSIST_MAX=0) must give the same iterates."""
+    torch = torch_mod
+    prob = case(name)
+    A = csr_matrix(prob)
+    d = O.jacobi_inverse_diagonal(A) if precond == "jacobi" else None
+    b = torch.from_numpy(prob.b).cuda()
+    xs = {}
+    for mode in ("persistent", "graph"):
+        if mode == "graph":
+            monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+        with make_solver(G, prob, op, precond) as S:
+            for variant in ("hs", "pr", "pipe_pr", "m", "pipe_m"):
+                res = S.solve(b, variant=variant, tol=0.0, maxit=20)
+                ref = O.solve(variant, A, prob.b, d=d, tol=0.0, maxit=20)
+                assert rel(res.x.cpu().numpy(), ref.x) <= ITER_TOL, (mode, variant)
+                xs[(mode, variant)] = res.x.cpu().numpy()
+                from paper_1905_01549_gb300 import binding
+                launches = binding.prcg_last_launches(S.handle)
+                assert (launches == 1) == (mode == "persistent"), (mode, launches)
+        monkeypatch.delenv("PRCG_PERSIST_MAX", raising=False)
