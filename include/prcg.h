@@ -226,6 +226,21 @@ const char* prcg_last_error(const prcg_ctx* ctx);
 /* prcg_n -- the number of unknowns of the context (or -1 for NULL). */
 int64_t prcg_n(const prcg_ctx* ctx);
 
+/*
+ * prcg_error_anorm -- the A-norm of the error, ||x* - x||_A =
+ * sqrt((x* - x)^T A (x* - x)), with the context's operator A (not the
+ * preconditioned one).  This is the error measure of the paper's
+ * convergence study (Section 4: iterations to reduce it by a factor 10^5,
+ * and its minimum over the run, Table 2).
+ *   x_star, x  length n, host or device (FP64); read only, borrowed
+ *   err_out    host double, receives the norm (a negative e^T A e from
+ *              rounding is reported as 0)
+ * Returns PRCG_OK or a negative error.  Uses the context's scratch vectors,
+ * so it must not overlap a prcg_solve on the same context; blocks until the
+ * value is on the host.
+ */
+int prcg_error_anorm(prcg_ctx* ctx, const double* x_star, const double* x, double* err_out);
+
 /* ------------------------------------------------------------------------
  * Batched solver: many independent SPD systems of uneven size in one launch.
  *

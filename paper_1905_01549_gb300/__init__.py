@@ -101,6 +101,14 @@ class Solver:
         _, loop_ms, _ = binding.prcg_last_timing(self.handle)
         return x, status, outer, inner, trr, hist[:outer + 1], loop_ms
 
+    def error_anorm(self, x_star, x) -> float:
+        """||x* - x||_A with this context's operator (Section 4's error measure)."""
+        if isinstance(x_star, np.ndarray):
+            x_star = np.ascontiguousarray(x_star, dtype=np.float64)
+        if isinstance(x, np.ndarray):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+        return binding.prcg_error_anorm(self.handle, x_star, x)
+
     def close(self):
         if self.handle:
             binding.prcg_destroy(self.handle)

@@ -31,7 +31,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_INVALID", 
 EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_solve", "prcg_last_timing",
            "prcg_time_sweeps", "prcg_solve_f32_refined", "prcg_update_faces",
            "prcg_grad_faces", "prcg_grad_csr_values",
-           "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n",
+           "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n", "prcg_error_anorm",
            "prcg_pr_solve_stencil_noalloc", "prcg_batched_create", "prcg_batched_configure",
            "prcg_batched_solve", "prcg_batched_last_ms", "prcg_batched_config",
            "prcg_batched_last_error", "prcg_batched_destroy")
@@ -91,6 +91,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.prcg_last_error.restype = ctypes.c_char_p
     lib.prcg_n.argtypes = [vp]
     lib.prcg_n.restype = ctypes.c_int64
+    lib.prcg_error_anorm.argtypes = [vp, vp, vp, _c_double_p]
+    lib.prcg_error_anorm.restype = ctypes.c_int
     lib.prcg_pr_solve_stencil_noalloc.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                                                   ctypes.c_int64, ctypes.c_double, ctypes.c_int,
                                                   vp, vp, ctypes.c_double, ctypes.c_int, vp,
@@ -233,6 +235,13 @@ def prcg_last_error(ctx=None) -> str:
 
 def prcg_n(ctx) -> int:
     return int(load().prcg_n(ctx))
+
+
+def prcg_error_anorm(ctx, x_star, x) -> float:
+    """||x* - x||_A with the context's operator (host or device arrays)."""
+    err = ctypes.c_double(0.0)
+    _check(load().prcg_error_anorm(ctx, ptr(x_star), ptr(x), ctypes.byref(err)), ctx)
+    return err.value
 
 
 def prcg_pr_solve_stencil_noalloc(dim, nx, ny, nz, diag_shift, precond, b, x, tol, maxit,

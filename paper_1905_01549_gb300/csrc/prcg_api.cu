@@ -1121,4 +1121,21 @@ const char* prcg_last_error(const prcg_ctx* c) {
 
 int64_t prcg_n(const prcg_ctx* c) { return c ? (int64_t)c->n : -1; }
 
+int prcg_error_anorm(prcg_ctx* c, const double* x_star, const double* x, double* err_out) {
+  if (!c) return set_err(nullptr, PRCG_ERR_INVALID, "ctx is NULL");
+  if (!x_star || !x || !err_out) return set_err(c, PRCG_ERR_INVALID, "NULL argument");
+  const size_t bytes = (size_t)c->n * sizeof(double);
+  int rc;
+  if ((rc = wait_user(c)) != PRCG_OK) return rc;
+  if ((rc = copy_in(c, c->plan.v.t, x_star, bytes)) != PRCG_OK) return rc;
+  if ((rc = copy_in(c, c->plan.v.w[1], x, bytes)) != PRCG_OK) return rc;
+  const cudaError_t e = c->launch(c->plan, PH_ANORM, V_PR, 0, 0, c->cs);
+  if (e != cudaSuccess) return cuda_err(c, e, "A-norm error");
+  DevState h;
+  CK(cudaMemcpyAsync(&h, c->S, sizeof h, cudaMemcpyDeviceToHost, c->cs));
+  CK(cudaStreamSynchronize(c->cs));
+  *err_out = sqrt(h.eta > 0.0 ? h.eta : 0.0);
+  return PRCG_OK;
+}
+
 }  // extern "C"

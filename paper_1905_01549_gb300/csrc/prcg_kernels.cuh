@@ -633,4 +633,19 @@ __global__ void __launch_bounds__(kBlock) k_true_res(Op op, Pc pc, Vecs V, DevSt
   }
 }
 
+// ||e||_A^2 = e^T A e with e = x* - x (x* in V.t, x in V.w[1]) into S->eta:
+// the error measure of the paper's convergence study (Section 4).
+template <class Op>
+__global__ void __launch_bounds__(kBlock) k_anorm(Op op, Vecs V, DevState* S, double* partials) {
+  double acc[1] = {0.0};
+  const double* __restrict__ xs = V.t;
+  const double* __restrict__ xx = V.w[1];
+  PRCG_ROWS(i, op.n) {
+    const double ae = op.row(i, [&](int j) { return __ldg(xs + j) - __ldg(xx + j); });
+    acc[0] = fma(__ldg(xs + i) - __ldg(xx + i), ae, acc[0]);
+  }
+  double tot[1];
+  if (grid_sum<1>(acc, partials, S, tot) && threadIdx.x == 0) S->eta = tot[0];
+}
+
 }  // namespace prcg

@@ -27,7 +27,8 @@ enum Phase {
   PH_CG_A = 15,
   PH_CG_B = 16,
   PH_GV = 17,
-  PH_PERSIST = 18   // the whole solve as one cooperative launch (HS, PR, M, pipe, pipe-M)
+  PH_PERSIST = 18,  // the whole solve as one cooperative launch (HS, PR, M, pipe, pipe-M)
+  PH_ANORM = 19     // ||x* - x||_A^2 (x* in V.t, x in V.w[1]) into S->eta
 };
 
 struct Plan {
@@ -133,11 +134,59 @@ cudaError_t launch_mixed(const Plan& P, int phase, cudaStream_t st) {
   }
 }
 
+// Dense operators: form the product a sweep needs before launching it (the
+// sweep's row() then reads the partial products).  No-op for other operators.
+template <class Op, class Pc>
+cudaError_t dense_prepass(const Plan& P, const Op& op, int phase, int qr, cudaStream_t st) {
+  if constexpr (!IsDense<Op>::value) {
+    return cudaSuccess;
+  } else {
+    const Vecs& V = P.v;
+    DenseSrc s0, s1;
+    int nv = 1, check = 1;
+    switch (phase) {
+      case PH_INIT_A: s0.a = V.x; break;
+      case PH_INIT_B:
+      case PH_HS_C:
+      case PH_PR_B: s0.a = V.p[0]; break;
+      case PH_PIPE:
+        s0.a = Pc::on ? V.st[qr] : V.s[qr];
+        s1.a = Pc::on ? V.rt[qr] : V.r[qr];
+        nv = 2;
+        break;
+      case PH_CG_B: s0.a = Pc::on ? V.rt[0] : V.r[0]; break;
+      case PH_GV:
+        s0.a = V.w[qr];
+        if (Pc::on) s0.scale = P.pc.d;
+        break;
+      case PH_TRUE_RES: s0.a = V.x; check = 0; break;
+      case PH_ANORM:
+        s0.a = V.t;
+        s0.sub = V.w[1];
+        check = 0;
+        break;
+      default: return cudaSuccess;
+    }
+    const long units = (long)((op.n + 31) / 32) * op.ncb;
+    long g = (units + kBlock / 32 - 1) / (kBlock / 32);
+    if (g > (long)P.sms * 8) g = (long)P.sms * 8;
+    if (nv == 2)
+      k_dense_product<2><<<(int)g, kBlock, 0, st>>>(op, P.S, s0, s1, check);
+    else
+      k_dense_product<1><<<(int)g, kBlock, 0, st>>>(op, P.S, s0, s1, check);
+    return cudaGetLastError();
+  }
+}
+
 template <class Op, class Pc>
 cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, cudaStream_t st) {
   Op op(P.op);
   Pc pc(P.pc);
   const int n = P.op.n;
+  if (phase != PH_PERSIST) {
+    const cudaError_t e = dense_prepass<Op, Pc>(P, op, phase, qr, st);
+    if (e != cudaSuccess) return e;
+  }
   const int meurant = (variant == V_M || variant == V_PIPE_M) ? 1 : 0;
   switch (phase) {
     case PH_INIT_A: {
@@ -228,6 +277,11 @@ cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, 
     case PH_TRUE_RES: {
       auto k = k_true_res<Op, Pc>;
       k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials);
+      break;
+    }
+    case PH_ANORM: {
+      auto k = k_anorm<Op>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, P.v, P.S, P.partials);
       break;
     }
     case PH_MX_RESID: {

@@ -12,7 +12,7 @@
 
 namespace prcg {
 
-enum OpKind { OP_CSR = 0, OP_ST2 = 1, OP_ST3 = 2, OP_VC2 = 3, OP_VC3 = 4, OP_SELL = 5 };
+enum OpKind { OP_CSR = 0, OP_ST2 = 1, OP_ST3 = 2, OP_VC2 = 3, OP_VC3 = 4, OP_SELL = 5, OP_DENSE = 6 };
 enum PcKind { PC_NONE = 0, PC_SCALAR = 1, PC_VEC = 2 };
 
 // Host-side description of an operator; the device structs below are built
@@ -35,6 +35,10 @@ struct OpDesc {
   const double* sval;    // SELL-32 values (padding: column = row, value 0)
   const float* sval32;   // FP32 copy of sval for the mixed-precision inner solve
   int tma;               // SELL-32 tiles fit the TMA stages: product sweeps stage entries in smem
+  const double* da;      // dense: A column-major (= row-major, A symmetric), leading dimension lda
+  int lda;               // dense: multiple of 32, >= n
+  int ncb, cbw;          // dense: column blocks of the product and their width
+  double* dpart[2];      // dense: partial products, [ncb][n] each
 };
 
 struct PcDesc {
@@ -117,37 +121,24 @@ struct SellOp {
       if (t < L) f(j[t], a[t]);
     for (int t = 8; t < L; ++t) f(__ldg(scol + base + 32 * t), __ldg(sval + base + 32 * t));
   }
-  // two interleaved accumulators halve the dependent FMA chain (an FP64 FMA
-  // has 64 cycles of latency on GB300)
+  // one FMA chain per row: the large sweeps are bound by FP64 issue, so a
+  // second accumulator (one more FP64 add per row) would cost more than the
+  // chain latency it hides
   template <class G>
   __device__ __forceinline__ double row(int i, G&& g) const {
-    double a0 = 0.0, a1 = 0.0;
-    int t = 0;
-    visit(i, [&](int j, double a) {
-      if (t & 1)
-        a1 = fma(a, g(j), a1);
-      else
-        a0 = fma(a, g(j), a0);
-      ++t;
-    });
-    return a0 + a1;
+    double acc = 0.0;
+    visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
+    return acc;
   }
   template <class G1, class G2>
   __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
-    double c1 = 0.0, c2 = 0.0, e1 = 0.0, e2 = 0.0;
-    int t = 0;
+    double c1 = 0.0, c2 = 0.0;
     visit(i, [&](int j, double a) {
-      if (t & 1) {
-        e1 = fma(a, g1(j), e1);
-        e2 = fma(a, g2(j), e2);
-      } else {
-        c1 = fma(a, g1(j), c1);
-        c2 = fma(a, g2(j), c2);
-      }
-      ++t;
+      c1 = fma(a, g1(j), c1);
+      c2 = fma(a, g2(j), c2);
     });
-    a1 = c1 + e1;
-    a2 = c2 + e2;
+    a1 = c1;
+    a2 = c2;
   }
 };
 
@@ -177,20 +168,14 @@ struct StencilOp {
     f(y < ny - 1 ? i + nx : i, y < ny - 1 ? -1.0 : 0.0);
     if (DIM == 3) f(z < nz - 1 ? i + pl : i, z < nz - 1 ? -1.0 : 0.0);
   }
-  // two interleaved accumulators halve the dependent FMA chain (an FP64 FMA
-  // has 64 cycles of latency on GB300)
+  // one FMA chain per row: the large sweeps are bound by FP64 issue, so a
+  // second accumulator (one more FP64 add per row) would cost more than the
+  // chain latency it hides
   template <class G>
   __device__ __forceinline__ double row(int i, G&& g) const {
-    double a0 = 0.0, a1 = 0.0;
-    int t = 0;
-    visit(i, [&](int j, double a) {
-      if (t & 1)
-        a1 = fma(a, g(j), a1);
-      else
-        a0 = fma(a, g(j), a0);
-      ++t;
-    });
-    return a0 + a1;
+    double acc = 0.0;
+    visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
+    return acc;
   }
   template <class G>
   __device__ __forceinline__ float row32(int i, G&& g) const {
@@ -200,20 +185,13 @@ struct StencilOp {
   }
   template <class G1, class G2>
   __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
-    double c1 = 0.0, c2 = 0.0, e1 = 0.0, e2 = 0.0;
-    int t = 0;
+    double c1 = 0.0, c2 = 0.0;
     visit(i, [&](int j, double a) {
-      if (t & 1) {
-        e1 = fma(a, g1(j), e1);
-        e2 = fma(a, g2(j), e2);
-      } else {
-        c1 = fma(a, g1(j), c1);
-        c2 = fma(a, g2(j), c2);
-      }
-      ++t;
+      c1 = fma(a, g1(j), c1);
+      c2 = fma(a, g2(j), c2);
     });
-    a1 = c1 + e1;
-    a2 = c2 + e2;
+    a1 = c1;
+    a2 = c2;
   }
 };
 
@@ -250,20 +228,14 @@ struct VarStencilOp {
     f(y < ny - 1 ? i + nx : i, y < ny - 1 ? -cyp : 0.0);
     if (DIM == 3) f(z < nz - 1 ? i + pl : i, z < nz - 1 ? -czp : 0.0);
   }
-  // two interleaved accumulators halve the dependent FMA chain (an FP64 FMA
-  // has 64 cycles of latency on GB300)
+  // one FMA chain per row: the large sweeps are bound by FP64 issue, so a
+  // second accumulator (one more FP64 add per row) would cost more than the
+  // chain latency it hides
   template <class G>
   __device__ __forceinline__ double row(int i, G&& g) const {
-    double a0 = 0.0, a1 = 0.0;
-    int t = 0;
-    visit(i, [&](int j, double a) {
-      if (t & 1)
-        a1 = fma(a, g(j), a1);
-      else
-        a0 = fma(a, g(j), a0);
-      ++t;
-    });
-    return a0 + a1;
+    double acc = 0.0;
+    visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
+    return acc;
   }
   template <class G>
   __device__ __forceinline__ float row32(int i, G&& g) const {
@@ -273,22 +245,52 @@ struct VarStencilOp {
   }
   template <class G1, class G2>
   __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
-    double c1 = 0.0, c2 = 0.0, e1 = 0.0, e2 = 0.0;
-    int t = 0;
+    double c1 = 0.0, c2 = 0.0;
     visit(i, [&](int j, double a) {
-      if (t & 1) {
-        e1 = fma(a, g1(j), e1);
-        e2 = fma(a, g2(j), e2);
-      } else {
-        c1 = fma(a, g1(j), c1);
-        c2 = fma(a, g2(j), c2);
-      }
-      ++t;
+      c1 = fma(a, g1(j), c1);
+      c2 = fma(a, g2(j), c2);
     });
-    a1 = c1 + e1;
-    a2 = c2 + e2;
+    a1 = c1;
+    a2 = c2;
   }
 };
+
+// ------------------------------------------------------------ dense matrix
+// Symmetric dense A (the paper's Section 5 model problem, stored dense to
+// make the two products of pipe-PR-CG cost a full pass over A).  A product
+// y = A v is formed before the sweep that needs it by dense_units()
+// (prcg_dense.cuh): warp units of 32 rows x one column block write partial
+// sums part[c][i]; row(i, .) then adds the ncb partials of row i in column
+// block order, so the result does not depend on the launch shape.  The
+// gather argument of row() is ignored -- the caller has already formed the
+// product of the vector that gather would read.
+struct DenseOp {
+  int n, lda, ncb, cbw;
+  const double* __restrict__ A;
+  double* part0;
+  double* part1;
+  explicit DenseOp(const OpDesc& o)
+      : n(o.n), lda(o.lda), ncb(o.ncb), cbw(o.cbw), A(o.da), part0(o.dpart[0]), part1(o.dpart[1]) {}
+  __device__ __forceinline__ double sum_parts(const double* part, int i) const {
+    double acc = __ldcg(part + i);
+    for (int c = 1; c < ncb; ++c) acc += __ldcg(part + (size_t)c * n + i);
+    return acc;
+  }
+  template <class G>
+  __device__ __forceinline__ double row(int i, G&&) const {
+    return sum_parts(part0, i);
+  }
+  template <class G1, class G2>
+  __device__ __forceinline__ void row2(int i, G1&&, G2&&, double& a1, double& a2) const {
+    a1 = sum_parts(part0, i);
+    a2 = sum_parts(part1, i);
+  }
+};
+
+template <class Op>
+struct IsDense : std::false_type {};
+template <>
+struct IsDense<DenseOp> : std::true_type {};
 
 // ------------------------------------------------------ preconditioners
 struct PcNone {

@@ -17,6 +17,7 @@
 // barrier.  The cooperative launch guarantees that all CTAs are resident.
 #pragma once
 
+#include "prcg_dense.cuh"
 #include "prcg_kernels.cuh"
 
 namespace prcg {
@@ -185,6 +186,28 @@ __device__ __forceinline__ void finish(DevState* S, int k, int status) {
 
 constexpr int kZeroRhs = -101;   // internal: b == 0
 
+// Dense operators: every warp of the grid forms its units of the product
+// with v0 (and v1), then a barrier makes the partials visible to the row
+// loop that follows.  Other operators gather inside the row loop: no-op.
+template <class Op>
+__device__ __forceinline__ bool persist_product(const Op& op, const double* v0, const double* v1,
+                                                GridBar* gb, unsigned& epoch) {
+  if constexpr (IsDense<Op>::value) {
+    DenseSrc s0, s1;
+    s0.a = v0;
+    s1.a = v1;
+    const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
+    const int nw = (int)(gridDim.x * (blockDim.x >> 5));
+    if (v1)
+      dense_units<2>(op, s0, s1, gw, nw);
+    else
+      dense_units<1>(op, s0, s1, gw, nw);
+    return grid_sync(gb, epoch);
+  } else {
+    return true;
+  }
+}
+
 // One persistent solve.  VARIANT: V_HS, V_PR (meurant -> M-CG), V_PIPE
 // (meurant -> pipe-PR-M-CG).
 template <class Op, class Pc, int VARIANT>
@@ -199,6 +222,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
   double* __restrict__ x = V.x;
   Bcast o;
   // ---- initialize(): r_0, r~_0, p_0; nu_0, rho_0, <b, b>
+  if (!persist_product(op, x, nullptr, gb, epoch)) {
+    finish(S, 0, -4);
+    return;
+  }
   double a3[3] = {0.0, 0.0, 0.0};
   PRCG_OWN_ROWS(i, rb) {
     const double ax = op.row(i, [&](int j) { return __ldcg(x + j); });
@@ -240,6 +267,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
   // s_0 = A p_0 (s~_0 stored for pipe), mu_0, sigma_0, gamma_0
   {
     const double* p0 = V.p[0];
+    if (!persist_product(op, p0, nullptr, gb, epoch)) {
+      finish(S, 0, -4);
+      return;
+    }
     double b3[3] = {0.0, 0.0, 0.0};
     PRCG_OWN_ROWS(i, rb) {
       const double s = op.row(i, [&](int j) { return __ldcg(p0 + j); });
@@ -312,6 +343,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       }
       // C: s_k = A p_k, mu_k -> alpha_k
       const double* pp = V.p[0];
+      if (!persist_product(op, pp, nullptr, gb, epoch)) {
+        finish(S, k, -4);
+        return;
+      }
       double c1[1] = {0.0};
       PRCG_OWN_ROWS(i, rb) {
         const double sn = op.row(i, [&](int j) { return __ldcg(pp + j); });
@@ -356,6 +391,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       // B: s_k = A p_k; mu_k, sigma_k, gamma_k
       const double* pp = V.p[0];
       const double* rtv = Pc::on ? V.rt[0] : V.r[0];
+      if (!persist_product(op, pp, nullptr, gb, epoch)) {
+        finish(S, k, -4);
+        return;
+      }
       PRCG_OWN_ROWS(i, rb) {
         const double sn = op.row(i, [&](int j) { return __ldcg(pp + j); });
         V.s[0][i] = sn;
@@ -384,6 +423,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       const double* st_o = Pc::on ? V.st[qr] : V.s[qr];
       const double* r_o = V.r[qr];
       const double* s_o = V.s[qr];
+      if (!persist_product(op, st_o, rt_o, gb, epoch)) {
+        finish(S, k, -4);
+        return;
+      }
       double a5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
       PRCG_OWN_ROWS(i, rb) {
         double u, w;
