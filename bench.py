@@ -348,6 +348,7 @@ def run_ours(args):
         line["mixed_precision"] = run_mixed(G, prob, args)
         line["autograd"] = run_autograd(G, args)
         line["convergence"] = run_convergence(G, args)
+        line["dense_model"] = run_dense(G, args)
         if world == 1:
             line["cpu_baseline"] = run_cpu_baseline(prob, variant, precond, args)
     S.close()
@@ -568,6 +569,46 @@ def run_convergence(G, args):
                        "min_log10_err": round(r["min_log10_err"], 2),
                        "paper": PAPER_TABLE2_MODEL_48_8_3[pc][v]} for v, r in st.items()}
     out["seconds"] = round(time.perf_counter() - t0, 2)
+    return out
+
+
+def run_dense(G, args):
+    """Section 5's workload on one GPU: the Eq. 4.1 model problem with
+    n = 10752, rho = 0.9, kappa = 1e6 stored as a dense matrix, no
+    preconditioner, 1000 iterations of each variant with only the main loop
+    timed (minimum over 3 runs), as the paper times it.  Per iteration the
+    product reads A once (n^2 x 8 B); pipe-PR-CG and pipe-M-CG form the
+    paired product [A s, A r] in that one pass, at twice the FP64 FMAs."""
+    import torch
+    import problems as P
+    n, iters = 10752, 1000
+    t0 = time.perf_counter()
+    A, b, _ = P.model_problem_on_device(n, 0.9, 1e6)
+    gen_s = time.perf_counter() - t0
+    S = G.Solver.from_dense(A)
+    del A
+    torch.cuda.empty_cache()
+    peak_hbm, _ = _peaks()
+    peak_fp = fp64_peak()
+    out = {"workload": "model problem Eq. 4.1, n=10752, rho=0.9, kappa=1e6, dense FP64, no precond",
+           "iterations": iters, "generation_s": round(gen_s, 1)}
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    for v in ("hs", "cgcg", "m", "pr", "gv", "pipe_m", "pipe_pr"):
+        best = None
+        for _ in range(3):
+            x.zero_()
+            res = S.solve(b, x0=x, variant=v, tol=0.0, maxit=iters)
+            if best is None or res.loop_ms < best.loop_ms:
+                best = res
+        k = max(best.iters, 1)
+        us = 1e3 * best.loop_ms / k
+        products = 2 if v in ("pipe_pr", "pipe_m") else 1
+        fma = products * float(n) * n
+        out[v] = {"us_per_iter": round(us, 2), "iters": best.iters, "status": best.status,
+                  "A_read_gbs": round(8.0 * n * n / (us * 1e-6) / 1e9, 1),
+                  "hbm_frac": round(8.0 * n * n / (us * 1e-6) / 1e9 / peak_hbm, 3),
+                  "fp64_frac": round(fma / (us * 1e-6) / peak_fp, 3)}
+    S.close()
     return out
 
 

@@ -108,6 +108,27 @@ int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t
                         void* cuda_stream);
 
 /*
+ * prcg_create_dense -- context for a dense symmetric positive definite A
+ * (Section 5 stores its model problem, Eq. 4.1, as a dense matrix so that
+ * pipe-PR-CG's two products per iteration cost a full pass over A).
+ *   n        1 <= n <= 131072
+ *   A        n x n FP64, row-major (for symmetric A also column-major), host
+ *            or device; copied into the context (column-major with a
+ *            leading dimension rounded up to 32), the caller keeps ownership.
+ *            Symmetry is not checked: the library forms A^T v.
+ *   precond  PRCG_PRECOND_NONE or PRCG_PRECOND_JACOBI (d_i = 1 / a_ii; a
+ *            non-positive diagonal entry gives PRCG_ERR_INVALID)
+ * Every product A v is formed by a pre-pass over A in column blocks whose
+ * partial sums each row then adds in block order (deterministic for a given
+ * n on a given GPU model).  Solves with n <= 4096 run as the persistent
+ * kernel of prcg_solve; larger ones as the graph with a product kernel
+ * before each product sweep.  All seven variants are supported;
+ * prcg_solve_f32_refined returns PRCG_ERR_UNSUPPORTED.
+ * Returns PRCG_OK, PRCG_ERR_INVALID, PRCG_ERR_OOM or PRCG_ERR_CUDA.
+ */
+int prcg_create_dense(prcg_ctx** out, int64_t n, const double* A, int precond, void* cuda_stream);
+
+/*
  * prcg_solve -- run one variant from x_0 until ||r_k|| / ||b|| <= tol.
  *   variant   prcg_variant
  *   b         double[n] right-hand side (host or device)
@@ -121,10 +142,11 @@ int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t
  * Returns PRCG_OK, PRCG_NOT_CONVERGED, PRCG_BREAKDOWN (x holds x_K in all
  * three) or a negative error (x untouched).  If b == 0, x is set to 0 and
  * K = 0.  The call blocks until the result is on the host.
- * Execution: for n <= 2^21 (environment PRCG_PERSIST_MAX overrides) HS, PR,
- * M, pipe-PR and pipe-M run as one persistent cooperative kernel (grid
- * barriers instead of kernel boundaries); larger systems, CG-CG and GV run
- * as one CUDA graph launch with a device-side while loop.
+ * Execution: for n <= 2^21 (dense contexts: n <= 4096; the environment
+ * variable PRCG_PERSIST_MAX lowers the bound) HS, PR, M, pipe-PR and pipe-M
+ * run as one persistent cooperative kernel (grid barriers instead of kernel
+ * boundaries); larger systems, CG-CG and GV run as one CUDA graph launch
+ * with a device-side while loop.
  */
 int prcg_solve(prcg_ctx* ctx, int variant, const double* b, double* x,
                double tol, int maxit, double* residual_history,

@@ -67,6 +67,18 @@ class Solver:
                                         PRECONDS[precond], stream)
         return cls(h, nx * ny * nz)
 
+    @classmethod
+    def from_dense(cls, A, precond: str = "none", stream=None) -> "Solver":
+        """Dense symmetric positive definite A (n x n numpy array or CUDA
+        tensor, row-major); the context keeps its own copy."""
+        n = int(A.shape[0])
+        if A.shape != (n, n):
+            raise ValueError("A must be square")
+        if isinstance(A, np.ndarray):
+            A = np.ascontiguousarray(A, dtype=np.float64)
+        h = binding.prcg_create_dense(n, A, PRECONDS[precond], stream)
+        return cls(h, n)
+
     def solve(self, b, x0=None, variant: str = "pr", tol: float = 1e-10,
               maxit: Optional[int] = None, history: bool = False,
               true_relres: bool = False) -> SolveResult:

@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_INVALID", 
                 -3: "ERR_OOM", -4: "ERR_TIMEOUT", -5: "ERR_UNSUPPORTED"}
 
 # every symbol include/prcg.h declares
-EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_solve", "prcg_last_timing",
+EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_create_dense", "prcg_solve", "prcg_last_timing",
            "prcg_time_sweeps", "prcg_solve_f32_refined", "prcg_update_faces",
            "prcg_grad_faces", "prcg_grad_csr_values",
            "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n", "prcg_error_anorm",
@@ -66,6 +66,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                         ctypes.c_int64, ctypes.c_int64, vp, ctypes.c_double,
                                         ctypes.c_int, vp]
     lib.prcg_create_stencil.restype = ctypes.c_int
+    lib.prcg_create_dense.argtypes = [ctypes.POINTER(vp), ctypes.c_int64, vp, ctypes.c_int, vp]
+    lib.prcg_create_dense.restype = ctypes.c_int
     lib.prcg_solve.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.c_int, vp,
                                _c_int_p, _c_double_p]
     lib.prcg_solve.restype = ctypes.c_int
@@ -164,6 +166,16 @@ def prcg_create_stencil(dim, nx, ny, nz, face_coeff=None, diag_shift=0.0,
     rc = lib.prcg_create_stencil(ctypes.byref(out), int(dim), int(nx), int(ny), int(nz),
                                  ptr(face_coeff), float(diag_shift), int(precond),
                                  _stream_ptr(stream))
+    _check(rc, None)
+    return out.value
+
+
+def prcg_create_dense(n, A, precond=PRCG_PRECOND_NONE, stream=None):
+    """Create a dense symmetric matrix context (A: n x n, row-major, host or
+    device); returns the opaque handle."""
+    lib = load()
+    out = ctypes.c_void_p()
+    rc = lib.prcg_create_dense(ctypes.byref(out), int(n), ptr(A), int(precond), _stream_ptr(stream))
     _check(rc, None)
     return out.value
 

@@ -24,10 +24,12 @@ namespace prcg {
 LaunchFn launcher_csr(int op_kind, int pc_kind);
 LaunchFn launcher_st(int op_kind, int pc_kind);
 LaunchFn launcher_vc(int op_kind, int pc_kind);
+LaunchFn launcher_dense(int op_kind, int pc_kind);
 
 LaunchFn launcher_for(int op_kind, int pc_kind) {
   if (op_kind == OP_CSR || op_kind == OP_SELL) return launcher_csr(op_kind, pc_kind);
   if (op_kind == OP_ST2 || op_kind == OP_ST3) return launcher_st(op_kind, pc_kind);
+  if (op_kind == OP_DENSE) return launcher_dense(op_kind, pc_kind);
   return launcher_vc(op_kind, pc_kind);
 }
 
@@ -59,6 +61,17 @@ __global__ void k_csr_jacobi(const int* rp, const int* ci, const double* va, int
     } else {
       d[i] = 1.0 / a;
     }
+  }
+}
+
+// d_i = 1 / a_ii of a dense matrix (column-major, leading dimension lda).
+__global__ void k_dense_jacobi(const double* A, int n, int lda, double* d, int* bad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const double a = A[(size_t)i * lda + i];
+    if (!(a > 0.0) || !isfinite(a))
+      atomicOr(bad, 4);
+    else
+      d[i] = 1.0 / a;
   }
 }
 
@@ -368,6 +381,10 @@ int launch_init(prcg_ctx* c, int variant, cudaStream_t st) {
 
 int init_launches(int) { return 2; }
 
+// Extra kernels per product sweep: dense operators form each product in a
+// pre-pass launch.
+int product_prepasses(const prcg_ctx* c) { return c->plan.op.kind == OP_DENSE ? 1 : 0; }
+
 // Kernels of one iteration of `variant`.
 int iter_launches(int variant) {
   switch (variant) {
@@ -515,7 +532,7 @@ int run_host_loop(prcg_ctx* c, int variant, int maxit) {
     for (int m = 0; m < chunk; ++m) {
       rc = launch_iter(c, variant, m & 1, (m + 1) & 1, c->cs);
       if (rc != PRCG_OK) return rc;
-      c->host_loop_launches += iter_launches(variant);
+      c->host_loop_launches += iter_launches(variant) + product_prepasses(c);
     }
   }
   CK(cudaEventRecord(c->ev_loop, c->cs));
@@ -712,6 +729,58 @@ int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t
   return PRCG_OK;
 }
 
+int prcg_create_dense(prcg_ctx** out, int64_t n, const double* A, int precond, void* cuda_stream) {
+  if (!out) return set_err(nullptr, PRCG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 1 || n > kMaxDenseN) return set_err(nullptr, PRCG_ERR_INVALID, "n out of range");
+  if (!A) return set_err(nullptr, PRCG_ERR_INVALID, "A is NULL");
+  if (precond != PRCG_PRECOND_NONE && precond != PRCG_PRECOND_JACOBI)
+    return set_err(nullptr, PRCG_ERR_INVALID, "unknown preconditioner");
+  prcg_ctx* c = new prcg_ctx();
+  int rc = ctx_init_common(c, cuda_stream, (int)n);
+  auto fail = [&](int code) {
+    g_create_error = c->err;
+    prcg_destroy(c);
+    return code;
+  };
+  if (rc != PRCG_OK) return fail(rc);
+  OpDesc& op = c->plan.op;
+  op.kind = OP_DENSE;
+  op.n = (int)n;
+  op.lda = (int)((n + 31) / 32 * 32);
+  // column blocks: about two warp units per warp of a one-CTA-per-SM grid,
+  // blocks of at least 128 columns
+  const long ng = (n + 31) / 32;
+  const long warps = (long)c->plan.sms * 32;
+  long ncb = (2 * warps + ng / 2) / ng;
+  ncb = std::max(1L, std::min(ncb, (long)((n + 127) / 128)));
+  op.cbw = (int)((n + ncb - 1) / ncb);
+  op.ncb = (int)((n + op.cbw - 1) / op.cbw);
+  const size_t na = (size_t)op.lda * (size_t)n, np = (size_t)op.ncb * (size_t)n;
+  if (cudaMalloc(&c->vpool, (na + 2 * np) * sizeof(double)) != cudaSuccess)
+    return fail(set_err(c, PRCG_ERR_OOM, "matrix allocation failed"));
+  if ((rc = wait_user(c)) != PRCG_OK) return fail(rc);
+  if (cudaMemcpy2DAsync(c->vpool, (size_t)op.lda * sizeof(double), A, (size_t)n * sizeof(double),
+                        (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDefault,
+                        c->cs) != cudaSuccess)
+    return fail(cuda_err(c, cudaGetLastError(), "copy of A"));
+  op.da = c->vpool;
+  op.dpart[0] = c->vpool + na;
+  op.dpart[1] = c->vpool + na + np;
+  c->precond = precond;
+  c->plan.pc.kind = PC_NONE;
+  if (precond == PRCG_PRECOND_JACOBI) {
+    k_dense_jacobi<<<c->plan.sms * 4, 256, 0, c->cs>>>(op.da, (int)n, op.lda,
+                                                       const_cast<double*>(c->plan.pc.d), c->dbad);
+    if ((rc = check_bad(c, "Jacobi needs a positive diagonal")) != PRCG_OK) return fail(rc);
+    c->plan.pc.kind = PC_VEC;
+  }
+  c->launch = launcher_for(op.kind, c->plan.pc.kind);
+  if (!c->launch) return fail(set_err(c, PRCG_ERR_UNSUPPORTED, "operator not built"));
+  *out = c;
+  return PRCG_OK;
+}
+
 int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol, int maxit,
                double* residual_history, int* iters_out, double* final_true_relres_out) {
   if (!c) return set_err(nullptr, PRCG_ERR_INVALID, "ctx is NULL");
@@ -727,8 +796,14 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
     CK(cudaMalloc(&c->hist, (size_t)(maxit + 1) * sizeof(double)));
     c->hist_cap = maxit + 1;
   }
-  // small and medium systems: the whole solve as one persistent cooperative launch
-  const bool persist = n <= c->persist_max &&
+  // small and medium systems: the whole solve as one persistent cooperative
+  // launch.  Dense matrices only while A is about L2-sized: beyond that the
+  // product dominates the iteration, and the stand-alone product kernel
+  // (8 CTAs of 256 threads per SM) outruns the persistent kernel's in-kernel
+  // product (one 1024-thread CTA per SM) by ~11 % at n = 10752.
+  const int persist_max =
+      c->plan.op.kind == OP_DENSE ? std::min(c->persist_max, kDensePersistMax) : c->persist_max;
+  const bool persist = n <= persist_max &&
                        (variant == V_HS || variant == V_PR || variant == V_M || variant == V_PIPE ||
                         variant == V_PIPE_M);
   bool graph = !persist && c->use_graph;
@@ -772,15 +847,15 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   CK(cudaStreamSynchronize(c->cs));
   const int K = h.k;
   {
-    const int64_t per_iter = iter_launches(variant);
-    int64_t launches = init_launches(variant);
+    const int64_t per_iter = iter_launches(variant) + product_prepasses(c);
+    int64_t launches = init_launches(variant) + 2 * product_prepasses(c);
     if (persisted)
       launches = 1;
     else if (graph)
       launches += (int64_t)h.bodies * (chunk * per_iter + 1);
     else
       launches += c->host_loop_launches;
-    if (final_true_relres_out) launches += 1;
+    if (final_true_relres_out) launches += 1 + product_prepasses(c);
     c->last_launches = launches;
   }
   const int status = h.status;
@@ -892,6 +967,8 @@ int prcg_solve_f32_refined(prcg_ctx* c, const double* b, double* x, double tol, 
   const int n = c->n;
   if (c->plan.op.kind == OP_CSR)
     return set_err(c, PRCG_ERR_UNSUPPORTED, "mixed precision needs the SELL-32 layout");
+  if (c->plan.op.kind == OP_DENSE)
+    return set_err(c, PRCG_ERR_UNSUPPORTED, "mixed precision is not built for dense matrices");
   if (!c->pool32) {
     CK(cudaMalloc(&c->pool32, 6 * (size_t)n * sizeof(float)));
     CK(cudaMalloc(&c->S2, sizeof(DevState)));

@@ -20,24 +20,30 @@
 
 namespace prcg {
 
-// The vector a product is formed with: v_j = scale_j * a_j - sub_j, the
-// optional terms absent when NULL (Jacobi's M^{-1} w of GV-CG, the error
-// x* - x of prcg_error_anorm).  Loads are coherent (L2): inside the
-// persistent solve the vector was written by other CTAs in the same launch.
+// The vector a product is formed with: v_j = a_j (DS_PLAIN), scale_j * a_j
+// (DS_SCALE: Jacobi's M^{-1} w of GV-CG) or a_j - sub_j (DS_SUB: the error
+// x* - x of prcg_error_anorm).  The form is a template argument: as a
+// run-time choice the compiler if-converts it into FP64 instructions on
+// every element, tripling the FP64 issue of the product.  Loads are coherent
+// (L2): inside the persistent solve the vector was written by other CTAs in
+// the same launch.
+enum DenseSrcMode { DS_PLAIN = 0, DS_SCALE = 1, DS_SUB = 2 };
+
 struct DenseSrc {
   const double* a = nullptr;
   const double* scale = nullptr;
   const double* sub = nullptr;
-  __device__ __forceinline__ double operator()(int j) const {
+  template <int MODE>
+  __device__ __forceinline__ double at(int j) const {
     double v = __ldcg(a + j);
-    if (scale) v = __ldcg(scale + j) * v;
-    if (sub) v = v - __ldcg(sub + j);
+    if constexpr (MODE == DS_SCALE) v = __ldcg(scale + j) * v;
+    if constexpr (MODE == DS_SUB) v = v - __ldcg(sub + j);
     return v;
   }
 };
 
 // Units gw, gw + nw, ... of the product(s) with s0 (and s1 when NV == 2).
-template <int NV>
+template <int NV, int MODE>
 __device__ __forceinline__ void dense_units(const DenseOp& op, const DenseSrc& s0,
                                             const DenseSrc& s1, int gw, int nw) {
   const int lane = threadIdx.x & 31;
@@ -55,8 +61,8 @@ __device__ __forceinline__ void dense_units(const DenseOp& op, const DenseSrc& s
     for (int j = j0; j < j1; ++j) {
       const double aij = __ldcs(col);   // streamed: A is read once per product
       col += op.lda;
-      a0 = fma(aij, s0(j), a0);
-      if (NV == 2) a1 = fma(aij, s1(j), a1);
+      a0 = fma(aij, s0.template at<MODE>(j), a0);
+      if (NV == 2) a1 = fma(aij, s1.template at<MODE>(j), a1);
     }
     op.part0[(size_t)c * op.n + i] = a0;
     if (NV == 2) op.part1[(size_t)c * op.n + i] = a1;
@@ -66,11 +72,11 @@ __device__ __forceinline__ void dense_units(const DenseOp& op, const DenseSrc& s
 // Stand-alone product launched before a sweep of the graph / host loop
 // paths.  With check_done the launch is a no-op once the run has finished
 // (the sweeps after convergence inside the last loop body).
-template <int NV>
+template <int NV, int MODE>
 __global__ void __launch_bounds__(kBlock) k_dense_product(DenseOp op, DevState* S, DenseSrc s0,
                                                           DenseSrc s1, int check_done) {
   if (check_done && __ldcg(&S->done)) return;
-  dense_units<NV>(op, s0, s1, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5),
+  dense_units<NV, MODE>(op, s0, s1, (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5),
                   (int)((gridDim.x * blockDim.x) >> 5));
 }
 

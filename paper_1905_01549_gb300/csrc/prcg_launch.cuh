@@ -171,9 +171,13 @@ cudaError_t dense_prepass(const Plan& P, const Op& op, int phase, int qr, cudaSt
     long g = (units + kBlock / 32 - 1) / (kBlock / 32);
     if (g > (long)P.sms * 8) g = (long)P.sms * 8;
     if (nv == 2)
-      k_dense_product<2><<<(int)g, kBlock, 0, st>>>(op, P.S, s0, s1, check);
+      k_dense_product<2, DS_PLAIN><<<(int)g, kBlock, 0, st>>>(op, P.S, s0, s1, check);
+    else if (s0.scale)
+      k_dense_product<1, DS_SCALE><<<(int)g, kBlock, 0, st>>>(op, P.S, s0, s1, check);
+    else if (s0.sub)
+      k_dense_product<1, DS_SUB><<<(int)g, kBlock, 0, st>>>(op, P.S, s0, s1, check);
     else
-      k_dense_product<1><<<(int)g, kBlock, 0, st>>>(op, P.S, s0, s1, check);
+      k_dense_product<1, DS_PLAIN><<<(int)g, kBlock, 0, st>>>(op, P.S, s0, s1, check);
     return cudaGetLastError();
   }
 }

@@ -264,6 +264,9 @@ struct VarStencilOp {
 // block order, so the result does not depend on the launch shape.  The
 // gather argument of row() is ignored -- the caller has already formed the
 // product of the vector that gather would read.
+constexpr int kMaxDenseN = 1 << 17;        // A of up to 137 GB
+constexpr int kDensePersistMax = 4096;     // dense solves up to this n run persistent
+
 struct DenseOp {
   int n, lda, ncb, cbw;
   const double* __restrict__ A;

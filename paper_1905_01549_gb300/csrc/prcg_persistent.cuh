@@ -199,9 +199,9 @@ __device__ __forceinline__ bool persist_product(const Op& op, const double* v0, 
     const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     const int nw = (int)(gridDim.x * (blockDim.x >> 5));
     if (v1)
-      dense_units<2>(op, s0, s1, gw, nw);
+      dense_units<2, DS_PLAIN>(op, s0, s1, gw, nw);
     else
-      dense_units<1>(op, s0, s1, gw, nw);
+      dense_units<1, DS_PLAIN>(op, s0, s1, gw, nw);
     return grid_sync(gb, epoch);
   } else {
     return true;

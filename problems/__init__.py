@@ -220,6 +220,38 @@ def model_problem(n: int = 48, rho: float = 0.8, kappa: float = 1e3,
     return DenseProblem(A, b, x_star, lam)
 
 
+def dense_lowrank_spd(n: int, rank: int, rng: np.random.Generator) -> DenseProblem:
+    """Dense SPD A = diag(delta) + U U^T / n, delta ~ U[1, 2], U Gaussian n x rank
+    (a dense matrix built in O(n^2 rank)); x* ~ U(-1, 1), b = A x*."""
+    delta = rng.uniform(1.0, 2.0, n)
+    U = rng.standard_normal((n, rank))
+    A = (U @ U.T) / n
+    A[np.diag_indices(n)] += delta
+    x_star = rng.uniform(-1.0, 1.0, n)
+    return DenseProblem(A, A @ x_star, x_star, np.empty(0))
+
+
+def model_problem_on_device(n: int, rho: float, kappa: float, device: str = "cuda"):
+    """The Eq. 4.1 model problem built on a GPU with torch (for sizes where a
+    host QR takes minutes, e.g. Section 5's n = 10752): the Gaussian is drawn
+    on the host from the seeded generator, Q from its QR (R-diagonal signs
+    fixed), A = Q diag(lambda) Q^T symmetrised, x* = 1/sqrt(n), b = A x*.
+    Returns (A, b, x_star) as FP64 tensors on `device`."""
+    import torch
+    rng = rng_for(f"model_{n}_{rho}_{kappa}")
+    G = torch.from_numpy(rng.standard_normal((n, n))).to(device)
+    Q, R = torch.linalg.qr(G)
+    del G
+    Q = Q * torch.sign(torch.diagonal(R))
+    del R
+    lam = torch.from_numpy(model_eigenvalues(n, rho, kappa)).to(device)
+    A = (Q * lam) @ Q.T
+    del Q
+    A = 0.5 * (A + A.T)
+    x_star = torch.full((n,), 1.0 / np.sqrt(n), dtype=torch.float64, device=device)
+    return A.contiguous(), A @ x_star, x_star
+
+
 def strakos_diagonal(n: int = 100_000, lam1: float = 1e-3, lamn: float = 1e3,
                      rho: float = 0.8) -> Tuple[np.ndarray, np.ndarray]:
     """Diagonal of the Eq. 4.1 spectrum and b = A (1/sqrt(n)) 1."""

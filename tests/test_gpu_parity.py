@@ -4,42 +4,17 @@ Bar (from the method's statement of the target): FP64 iterates within 1e-10
 relative of the oracle over the first 20 iterations, the iteration count to
 the tolerance within 5 %, and the final true residual at the tolerance.
 """
-import math
-
 import numpy as np
 import pytest
 
 import oracle as O
-from gpu_common import CASES, GPU_VARIANTS, case, csr_matrix, make_solver, rel
+from gpu_common import CASES, GPU_VARIANTS, case, csr_matrix, make_solver, oracle_spread, rel
 
 pytestmark = pytest.mark.gpu
 
 ITER_TOL = 1e-10     # relative, first 20 iterations
 HIST_TOL = 1e-9      # per entry of ||r_k|| / ||b||
 SPREAD_FACTOR = 100.0
-
-
-def _fsum_dot(a, b):
-    return math.fsum(a * b)
-
-
-def oracle_spread(variant, A, b, d, k):
-    """Rounding sensitivity of the iterates themselves: the oracle against the
-    same oracle with exactly rounded inner products (math.fsum).  On
-    ill-conditioned systems (unpreconditioned log-normal diffusion, sigma = 2)
-    a change of summation order alone moves x_20 by up to ~1e-3, so no FP64
-    implementation can match another to 1e-10 there; the bar becomes
-    max(1e-10, 100 x this spread)."""
-    import oracle.cg_variants as CV
-    ref = O.solve(variant, A, b, d=d, tol=0.0, maxit=k)
-    saved = CV._dot
-    CV._dot = lambda u, v: saved(u, v) if u.dtype == object else _fsum_dot(u, v)
-    try:
-        alt = O.solve(variant, A, b, d=d, tol=0.0, maxit=k)
-    finally:
-        CV._dot = saved
-    hs = np.asarray(ref.hist)
-    return ref, rel(alt.x, ref.x), np.max(np.abs(np.asarray(alt.hist) - hs) / hs)
 
 
 @pytest.fixture(scope="module")
