@@ -219,10 +219,16 @@ def make_solver(G, prob, op, precond):
                                  precond=precond)
 
 
+# Sources that define the SELL-32 sweeps and their launch configuration (the
+# kernels whose DRAM traffic profiles/traffic.json records).
+SWEEP_SOURCES = ("prcg_common.cuh", "prcg_reduce.cuh", "prcg_ops.cuh", "prcg_kernels.cuh",
+                 "prcg_tma.cuh", "prcg_launch.cuh", "prcg_inst_csr.cu")
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1905_01549_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in SWEEP_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
