@@ -249,6 +249,25 @@ const char* prcg_last_error(const prcg_ctx* ctx);
 int64_t prcg_n(const prcg_ctx* ctx);
 
 /*
+ * prcg_trace_enable -- record, during every later prcg_solve on ctx (on != 0)
+ * or no more (on == 0), the scalars each iteration forms.  Costs a few
+ * device stores per iteration and a buffer of (maxit + 2) x 10 doubles.
+ *
+ * prcg_trace_get -- copy the trace of the last solve to out (host or device,
+ * slots x 10 doubles); returns the number of slots copied (<= slots; K + 1
+ * after a solve of K iterations) or a negative error.  Slot k, fields in
+ * order: alpha_{k-1} (the step length applied in iteration k), beta_k,
+ * nu_k, nu'_k (the predicted nu of Eq. 2.3 / Meurant's form), mu_k,
+ * sigma_k, gamma_k, rho_k = <r_k, r_k>, eta_k (CG-CG, GV-CG), unused.
+ * Slot 0 holds initialize()'s nu_0, mu_0, sigma_0, gamma_0, rho_0.  Fields a
+ * variant does not form are NaN, and so are those of slot K that follow the
+ * stopping test (beta_K, mu_K of HS-CG, for instance).  The paper has no counterpart: this exposes the
+ * quantities its analysis (Section 3) reasons about, for tests and studies.
+ */
+int prcg_trace_enable(prcg_ctx* ctx, int on);
+int prcg_trace_get(prcg_ctx* ctx, double* out, int slots);
+
+/*
  * prcg_error_anorm -- the A-norm of the error, ||x* - x||_A =
  * sqrt((x* - x)^T A (x* - x)), with the context's operator A (not the
  * preconditioned one).  This is the error measure of the paper's

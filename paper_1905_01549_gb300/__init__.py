@@ -31,6 +31,7 @@ class SolveResult:
     true_relres: Optional[float]
     init_ms: float
     loop_ms: float
+    trace: Optional[np.ndarray] = None   # (K + 1, 10) scalars per iteration, see prcg.h
 
 
 def _torch():
@@ -81,7 +82,7 @@ class Solver:
 
     def solve(self, b, x0=None, variant: str = "pr", tol: float = 1e-10,
               maxit: Optional[int] = None, history: bool = False,
-              true_relres: bool = False) -> SolveResult:
+              true_relres: bool = False, trace: bool = False) -> SolveResult:
         """Solve A x = b.  b / x0 may be CUDA tensors, CPU tensors or numpy arrays.
 
         Without x0 a zero CUDA tensor is used and returned as x; with x0 the
@@ -93,11 +94,18 @@ class Solver:
             b = np.ascontiguousarray(b, dtype=np.float64)
         x = x0 if x0 is not None else torch.zeros(self.n, dtype=torch.float64, device="cuda")
         hist = np.empty(maxit + 1) if history else None
-        status, iters, trr = binding.prcg_solve(self.handle, VARIANT_IDS[variant], b, x, tol, maxit,
-                                                hist, true_relres)
+        if trace:
+            binding.prcg_trace_enable(self.handle, True)
+        try:
+            status, iters, trr = binding.prcg_solve(self.handle, VARIANT_IDS[variant], b, x, tol,
+                                                    maxit, hist, true_relres)
+            tr = binding.prcg_trace_get(self.handle, maxit + 2) if trace else None
+        finally:
+            if trace:
+                binding.prcg_trace_enable(self.handle, False)
         init_ms, loop_ms, _ = binding.prcg_last_timing(self.handle)
         return SolveResult(x, iters, status, None if hist is None else hist[:iters + 1], trr,
-                           init_ms, loop_ms)
+                           init_ms, loop_ms, tr)
 
     def solve_refined_fp32(self, b, x0=None, tol: float = 1e-8, max_outer: int = 30,
                            inner_tol: float = 1e-4, inner_maxit: Optional[int] = None):

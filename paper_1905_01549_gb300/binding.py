@@ -32,6 +32,7 @@ EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_create_dense", "prcg_
            "prcg_time_sweeps", "prcg_solve_f32_refined", "prcg_update_faces",
            "prcg_grad_faces", "prcg_grad_csr_values",
            "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n", "prcg_error_anorm",
+           "prcg_trace_enable", "prcg_trace_get",
            "prcg_pr_solve_stencil_noalloc", "prcg_batched_create", "prcg_batched_configure",
            "prcg_batched_solve", "prcg_batched_last_ms", "prcg_batched_config",
            "prcg_batched_last_error", "prcg_batched_destroy")
@@ -95,6 +96,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.prcg_n.restype = ctypes.c_int64
     lib.prcg_error_anorm.argtypes = [vp, vp, vp, _c_double_p]
     lib.prcg_error_anorm.restype = ctypes.c_int
+    lib.prcg_trace_enable.argtypes = [vp, ctypes.c_int]
+    lib.prcg_trace_enable.restype = ctypes.c_int
+    lib.prcg_trace_get.argtypes = [vp, vp, ctypes.c_int]
+    lib.prcg_trace_get.restype = ctypes.c_int
     lib.prcg_pr_solve_stencil_noalloc.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
                                                   ctypes.c_int64, ctypes.c_double, ctypes.c_int,
                                                   vp, vp, ctypes.c_double, ctypes.c_int, vp,
@@ -247,6 +252,21 @@ def prcg_last_error(ctx=None) -> str:
 
 def prcg_n(ctx) -> int:
     return int(load().prcg_n(ctx))
+
+
+TRACE_FIELDS = ("alpha", "beta", "nu", "nu_pred", "mu", "sigma", "gamma", "rho", "eta", "unused")
+
+
+def prcg_trace_enable(ctx, on: bool):
+    _check(load().prcg_trace_enable(ctx, 1 if on else 0), ctx)
+
+
+def prcg_trace_get(ctx, slots: int) -> np.ndarray:
+    """The last solve's scalar trace as a (slots', 10) array (see prcg.h)."""
+    out = np.empty((max(slots, 0), len(TRACE_FIELDS)))
+    m = load().prcg_trace_get(ctx, ptr(out), int(slots))
+    _check(m if m < 0 else 0, ctx)
+    return out[:m]
 
 
 def prcg_error_anorm(ctx, x_star, x) -> float:

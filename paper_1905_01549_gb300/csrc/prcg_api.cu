@@ -260,6 +260,10 @@ struct prcg_ctx {
   DevState* S2 = nullptr;        // scalar block of the inner solve
   GridBar* gb = nullptr;         // grid barrier of the persistent solve
   int persist_max = 1 << 21;     // largest n solved by the persistent kernel
+  bool trace_on = false;         // record the scalar trace of each solve
+  double* trace = nullptr;       // device, trace_cap slots x kTraceFields
+  int trace_cap = 0;
+  int trace_slots = 0;           // slots written by the last solve (K + 2)
   std::string err;
 };
 
@@ -817,6 +821,19 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   h.tol = tol;
   h.tol2 = tol * tol;
   h.hist = c->hist;
+  c->trace_slots = 0;
+  if (c->trace_on) {
+    if (c->trace_cap < maxit + 2) {
+      if (c->trace) cudaFree(c->trace);
+      c->trace = nullptr;
+      c->trace_cap = 0;
+      CK(cudaMalloc(&c->trace, (size_t)(maxit + 2) * kTraceFields * sizeof(double)));
+      c->trace_cap = maxit + 2;
+    }
+    // all-ones bytes: every unset field reads as NaN
+    CK(cudaMemsetAsync(c->trace, 0xFF, (size_t)(maxit + 2) * kTraceFields * sizeof(double), c->cs));
+    h.trace = c->trace;
+  }
   h.maxit = maxit;
   h.maxbodies = maxit / chunk + 3;
   h.status = kRunning;
@@ -897,6 +914,7 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   c->t_init = ti;
   c->t_loop = tl;
   c->last_iters = K;
+  if (c->trace_on) c->trace_slots = K + 1;
   if (iters_out) *iters_out = K;
   return status;
 }
@@ -1181,6 +1199,7 @@ int prcg_destroy(prcg_ctx* c) {
   if (c->S) cudaFree(c->S);
   if (c->hS) cudaFreeHost(c->hS);
   if (c->hist) cudaFree(c->hist);
+  if (c->trace) cudaFree(c->trace);
   if (c->dbad) cudaFree(c->dbad);
   if (c->ev_user) cudaEventDestroy(c->ev_user);
   if (c->ev_start) cudaEventDestroy(c->ev_start);
@@ -1197,6 +1216,25 @@ const char* prcg_last_error(const prcg_ctx* c) {
 }
 
 int64_t prcg_n(const prcg_ctx* c) { return c ? (int64_t)c->n : -1; }
+
+int prcg_trace_enable(prcg_ctx* c, int on) {
+  if (!c) return set_err(nullptr, PRCG_ERR_INVALID, "ctx is NULL");
+  c->trace_on = on != 0;
+  c->trace_slots = 0;
+  return PRCG_OK;
+}
+
+int prcg_trace_get(prcg_ctx* c, double* out, int slots) {
+  if (!c) return set_err(nullptr, PRCG_ERR_INVALID, "ctx is NULL");
+  if (!out || slots < 0) return set_err(c, PRCG_ERR_INVALID, "bad argument");
+  const int m = std::min(slots, c->trace_slots);
+  if (m > 0) {
+    CK(cudaMemcpyAsync(out, c->trace, (size_t)m * kTraceFields * sizeof(double), cudaMemcpyDefault,
+                       c->cs));
+    CK(cudaStreamSynchronize(c->cs));
+  }
+  return m;
+}
 
 int prcg_error_anorm(prcg_ctx* c, const double* x_star, const double* x, double* err_out) {
   if (!c) return set_err(nullptr, PRCG_ERR_INVALID, "ctx is NULL");

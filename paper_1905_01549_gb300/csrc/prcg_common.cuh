@@ -43,7 +43,22 @@ struct DevState {
   unsigned bodies;       // executions of the while-loop body
   int profile;           // timing runs: never finish, keep every sweep doing its work
   double arg;            // mixed precision: 1 / ||t|| of the current refinement step
+  double* trace;         // optional scalar trace, (maxit + 2) x kTraceFields, or NULL
 };
+
+// Scalar trace: slot k holds the scalars of iteration k in the oracle's
+// convention -- alpha_{k-1} (applied in iteration k), beta_k, nu_k, nu'_k,
+// mu_k, sigma_k, gamma_k, rho_k = <r_k, r_k>, eta_k -- slot 0 those of
+// initialize().  Unset fields keep the host's fill (NaN).
+enum TraceField {
+  TR_ALPHA = 0, TR_BETA, TR_NU, TR_NU_PRED, TR_MU, TR_SIGMA, TR_GAMMA, TR_RHO, TR_ETA,
+  kTraceFields = 10
+};
+
+__device__ __forceinline__ void trace(const DevState* S, int k, int f, double v) {
+  double* t = S->trace;
+  if (t && k >= 0 && k <= S->maxit + 1) t[(size_t)k * kTraceFields + f] = v;
+}
 
 // Pointers of one context; kernels take what they need by value.
 struct Vecs {
@@ -170,6 +185,18 @@ __device__ __forceinline__ void scalar_step_pr(DevState* S, bool meurant) {
   S->alpha = alpha;
   S->nu_pred = nu_pred;
   S->beta = nu_pred / nu;
+  trace(S, S->k + 1, TR_ALPHA, alpha);
+  trace(S, S->k + 1, TR_NU_PRED, nu_pred);
+  trace(S, S->k + 1, TR_BETA, S->beta);
+}
+
+// The reduction of iteration k of PR-CG / pipe-PR-CG (values already in S).
+__device__ __forceinline__ void trace_pr_sums(const DevState* S, int k) {
+  trace(S, k, TR_NU, S->nu);
+  trace(S, k, TR_MU, S->mu);
+  trace(S, k, TR_SIGMA, S->sigma);
+  trace(S, k, TR_GAMMA, S->gamma);
+  trace(S, k, TR_RHO, S->rho);
 }
 
 }  // namespace prcg

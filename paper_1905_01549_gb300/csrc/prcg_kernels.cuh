@@ -54,6 +54,8 @@ __global__ void __launch_bounds__(kBlock) k_init_a(Op op, Pc pc, Vecs V, DevStat
     S->rho = tot[1];
     S->bnorm2 = tot[2];
     S->k = 0;
+    trace(S, 0, TR_NU, tot[0]);
+    trace(S, 0, TR_RHO, tot[1]);
     if (tot[2] == 0.0) {
       S->zero_rhs = 1;
       if (S->hist) S->hist[0] = 0.0;
@@ -94,6 +96,9 @@ __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevStat
     S->mu = tot[0];
     S->sigma = tot[1];
     S->gamma = tot[2];
+    trace(S, 0, TR_MU, tot[0]);
+    trace(S, 0, TR_SIGMA, tot[1]);
+    trace(S, 0, TR_GAMMA, tot[2]);
     if (variant == V_PR || variant == V_PIPE || variant == V_M || variant == V_PIPE_M) {
       scalar_step_pr(S, variant == V_M || variant == V_PIPE_M);
     } else {
@@ -102,6 +107,7 @@ __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevStat
         breakdown(S);
       } else {
         S->alpha = nu / mu;
+        trace(S, 1, TR_ALPHA, S->alpha);
         // CG-CG / GV-CG: the first sweep "updates" p_0, s_0 (, s~_0, u_0)
         // with beta_0 = 0, which leaves the initial vectors as they are
         S->beta = 0.0;
@@ -138,12 +144,15 @@ __global__ void __launch_bounds__(kBlock) k_hs_a(Op op, Pc pc, Vecs V, DevState*
     if (!Pc::on) nu = tot[1];
     if (std::is_same<Pc, PcScalar>::value) nu = pc(0) * tot[1];
     S->rho = tot[1];
+    trace(S, k, TR_NU, nu);
+    trace(S, k, TR_RHO, tot[1]);
     if (!record_and_test(S, k, tot[1])) {
       if (!finite(nu) || !(nu > 0.0)) {
         breakdown(S);
       } else {
         S->beta = nu / S->nu;
         S->nu = nu;
+        trace(S, k, TR_BETA, S->beta);
       }
     }
   }
@@ -179,10 +188,12 @@ __global__ void __launch_bounds__(kBlock) k_hs_c(Op op, Pc pc, Vecs V, DevState*
   if (grid_sum<1>(acc, partials, S, tot) && threadIdx.x == 0) {
     const double mu = tot[0];
     S->mu = mu;
+    trace(S, S->k, TR_MU, mu);
     if (!finite(mu) || !(mu > 0.0)) {
       breakdown(S);
     } else {
       S->alpha = S->nu / mu;
+      trace(S, S->k + 1, TR_ALPHA, S->alpha);
     }
   }
 }
@@ -267,6 +278,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_b(Op op, Pc pc, Vecs V, DevState*
     S->gamma = std::is_same<Pc, PcScalar>::value ? pc(0) * tot[2] : tot[2];
     S->nu = nu;
     S->rho = rho;
+    trace_pr_sums(S, k);
     if (!record_and_test(S, k, rho)) scalar_step_pr(S, meurant != 0);
   }
 }
@@ -333,6 +345,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
     S->gamma = tot[2];
     S->nu = tot[3];
     S->rho = tot[4];
+    trace_pr_sums(S, k);
     if (!record_and_test(S, k, tot[4])) scalar_step_pr(S, meurant != 0);
   }
 }
@@ -346,6 +359,9 @@ __device__ __forceinline__ void scalar_step_cg(DevState* S, int k, double nu, do
                                                double rho) {
   S->rho = rho;
   S->eta = eta;
+  trace(S, k, TR_NU, nu);
+  trace(S, k, TR_ETA, eta);
+  trace(S, k, TR_RHO, rho);
   if (record_and_test(S, k, rho)) return;
   if (!finite(nu) || !(nu > 0.0)) { breakdown(S); return; }
   const double beta = nu / S->nu;
@@ -355,6 +371,9 @@ __device__ __forceinline__ void scalar_step_cg(DevState* S, int k, double nu, do
   S->mu = mu;
   S->nu = nu;
   S->alpha = nu / mu;
+  trace(S, k, TR_BETA, beta);
+  trace(S, k, TR_MU, mu);
+  trace(S, k + 1, TR_ALPHA, S->alpha);
 }
 
 // Sweep A of CG-CG iteration k: finish iteration k-1 (p_{k-1} = r~_{k-1} +

@@ -164,6 +164,19 @@ __device__ __forceinline__ void pr_scalars(double nu, double mu, double sigma, d
   }
   o.d[0] = alpha;
   o.d[1] = np / nu;
+  o.d[2] = np;
+}
+
+// Trace writes of the persistent solve: the first thread of CTA 0 only.
+__device__ __forceinline__ void ptrace(const DevState* S, int k, int f, double v) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) trace(S, k, f, v);
+}
+
+__device__ __forceinline__ void ptrace_pr_step(const DevState* S, int k, const Bcast& q) {
+  if (q.status != kRunning) return;
+  ptrace(S, k + 1, TR_ALPHA, q.d[0]);
+  ptrace(S, k + 1, TR_BETA, q.d[1]);
+  ptrace(S, k + 1, TR_NU_PRED, q.d[2]);
 }
 
 // Stopping test of iteration k, ||r_k||^2 <= tol^2 ||b||^2 (no square root or
@@ -244,6 +257,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         const double bn2 = t[2];
         q.d[0] = t[0];
         q.d[1] = tol2 * bn2;
+        ptrace(S, 0, TR_NU, t[0]);
+        ptrace(S, 0, TR_RHO, t[1]);
         if (blockIdx.x == 0 && threadIdx.x == 0) S->bnorm2 = bn2;
         if (bn2 == 0.0) {
           if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -283,13 +298,19 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       b3[2] = fma(st, s, b3[2]);
     }
     if (!grid_sync_sum<3>(b3, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
+          ptrace(S, 0, TR_MU, t[0]);
+          ptrace(S, 0, TR_SIGMA, t[1]);
+          ptrace(S, 0, TR_GAMMA, t[2]);
           if (VARIANT == V_HS) {
-            if (!finite(nu) || !finite(t[0]) || !(t[0] > 0.0) || nu < 0.0)
+            if (!finite(nu) || !finite(t[0]) || !(t[0] > 0.0) || nu < 0.0) {
               q.status = 2;
-            else
+            } else {
               q.d[0] = nu / t[0];
+              ptrace(S, 1, TR_ALPHA, q.d[0]);
+            }
           } else {
             pr_scalars(nu, t[0], t[1], t[2], meurant != 0, q);
+            ptrace_pr_step(S, 0, q);
           }
         })) {
       finish(S, 0, -4);
@@ -314,6 +335,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         a2[1] = fma(rn, rn, a2[1]);
       }
       if (!grid_sync_sum<2>(a2, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
+            ptrace(S, k, TR_NU, t[0]);
+            ptrace(S, k, TR_RHO, t[1]);
             q.status = stop_test(S, k, t[1], stop2, maxit);
             if (q.status != kRunning) return;
             if (!finite(t[0]) || !(t[0] > 0.0)) {
@@ -322,6 +345,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             }
             q.d[0] = t[0] / nu;   // beta_k
             q.d[1] = t[0];        // nu_k
+            ptrace(S, k, TR_BETA, q.d[0]);
           })) {
         finish(S, k, -4);
         return;
@@ -354,10 +378,13 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         c1[0] = fma(pp[i], sn, c1[0]);
       }
       if (!grid_sync_sum<1>(c1, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
-            if (!finite(t[0]) || !(t[0] > 0.0))
+            ptrace(S, k, TR_MU, t[0]);
+            if (!finite(t[0]) || !(t[0] > 0.0)) {
               q.status = 2;
-            else
+            } else {
               q.d[0] = nu / t[0];
+              ptrace(S, k + 1, TR_ALPHA, q.d[0]);
+            }
           })) {
         finish(S, k, -4);
         return;
@@ -403,9 +430,15 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         a5[4] = fma(Pc::on ? pc(i) * sn : sn, sn, a5[4]);
       }
       if (!grid_sync_sum<5>(a5, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
+            ptrace(S, k, TR_NU, Pc::on ? t[0] : t[1]);
+            ptrace(S, k, TR_RHO, t[1]);
+            ptrace(S, k, TR_MU, t[2]);
+            ptrace(S, k, TR_SIGMA, t[3]);
+            ptrace(S, k, TR_GAMMA, t[4]);
             q.status = stop_test(S, k, t[1], stop2, maxit);
             if (q.status != kRunning) return;
             pr_scalars(Pc::on ? t[0] : t[1], t[2], t[3], t[4], meurant != 0, q);
+            ptrace_pr_step(S, k, q);
           })) {
         finish(S, k, -4);
         return;
@@ -462,9 +495,15 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         a5[4] = fma(rn, rn, a5[4]);
       }
       if (!grid_sync_sum<5>(a5, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
+            ptrace(S, k, TR_MU, t[0]);
+            ptrace(S, k, TR_SIGMA, t[1]);
+            ptrace(S, k, TR_GAMMA, t[2]);
+            ptrace(S, k, TR_NU, t[3]);
+            ptrace(S, k, TR_RHO, t[4]);
             q.status = stop_test(S, k, t[4], stop2, maxit);
             if (q.status != kRunning) return;
             pr_scalars(t[3], t[0], t[1], t[2], meurant != 0, q);
+            ptrace_pr_step(S, k, q);
           })) {
         finish(S, k, -4);
         return;

@@ -184,10 +184,12 @@ __global__ void __launch_bounds__(kBlock) k_hs_c_tma(SellOp op, Pc pc, Vecs V, D
   if (grid_sum<1>(acc, partials, S, tot) && threadIdx.x == 0) {
     const double mu = tot[0];
     S->mu = mu;
+    trace(S, S->k, TR_MU, mu);
     if (!finite(mu) || !(mu > 0.0)) {
       breakdown(S);
     } else {
       S->alpha = S->nu / mu;
+      trace(S, S->k + 1, TR_ALPHA, S->alpha);
     }
   }
 }
@@ -234,6 +236,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_b_tma(SellOp op, Pc pc, Vecs V, D
     S->gamma = tot[2];
     S->nu = nu;
     S->rho = rho;
+    trace_pr_sums(S, k);
     if (!record_and_test(S, k, rho)) scalar_step_pr(S, meurant != 0);
   }
 }
@@ -298,6 +301,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe_tma(SellOp op, Pc pc, Vecs V, D
     S->gamma = tot[2];
     S->nu = tot[3];
     S->rho = tot[4];
+    trace_pr_sums(S, k);
     if (!record_and_test(S, k, tot[4])) scalar_step_pr(S, meurant != 0);
   }
 }
