@@ -249,6 +249,31 @@ const char* prcg_last_error(const prcg_ctx* ctx);
 int64_t prcg_n(const prcg_ctx* ctx);
 
 /*
+ * prcg_inject_barrier_skip -- failure injection for tests: in the next
+ * prcg_solve that runs as the persistent kernel, CTA `cta` does not arrive
+ * at grid barrier number `barrier` (0 = the first of the solve), and every
+ * barrier wait gives up after `spin_limit` polls (>= 1024) instead of the
+ * default 2^22.  All CTAs then stop at that barrier, the solve returns
+ * PRCG_ERR_TIMEOUT with x untouched, and the context stays usable.  Nothing
+ * faults or hangs: every wait in the kernel is bounded.  One-shot; the paper
+ * has no counterpart.
+ */
+int prcg_inject_barrier_skip(prcg_ctx* ctx, int cta, int barrier, int64_t spin_limit);
+
+/*
+ * prcg_check_guards -- count corrupted guard words.  Every vector, partial
+ * sum buffer and scratch array of the context is followed by a 256-byte
+ * guard band (its rounding up to a multiple of 32 entries included; the
+ * vector pool also starts with one) holding a signalling-NaN bit pattern,
+ * which FP64 arithmetic never produces.  A kernel writing past the end of
+ * any of them changes a guard word.  *corrupted_out receives the number of
+ * changed words (0 when every access stayed in bounds).  A test utility in
+ * place of a memory checker; the paper has no counterpart.  Returns PRCG_OK
+ * or a negative error; blocks until the count is on the host.
+ */
+int prcg_check_guards(prcg_ctx* ctx, int64_t* corrupted_out);
+
+/*
  * prcg_trace_enable -- record, during every later prcg_solve on ctx (on != 0)
  * or no more (on == 0), the scalars each iteration forms.  Costs a few
  * device stores per iteration and a buffer of (maxit + 2) x 10 doubles.

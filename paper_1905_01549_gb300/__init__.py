@@ -9,6 +9,7 @@ has not been built (``paper_1905_01549_gb300.build.build()``).
 from __future__ import annotations
 
 import dataclasses
+import os
 from typing import Optional, Sequence
 
 import numpy as np
@@ -129,10 +130,24 @@ class Solver:
             x = np.ascontiguousarray(x, dtype=np.float64)
         return binding.prcg_error_anorm(self.handle, x_star, x)
 
+    def check_guards(self) -> int:
+        """Corrupted guard words (prcg_check_guards); 0 when every kernel
+        stayed within its buffers."""
+        return binding.prcg_check_guards(self.handle)
+
     def close(self):
         if self.handle:
-            binding.prcg_destroy(self.handle)
-            self.handle = None
+            h, self.handle = self.handle, None
+            try:
+                # test runs set PRCG_CHECK_GUARDS=1: every context is checked
+                # for out-of-bounds writes before it is freed
+                if os.environ.get("PRCG_CHECK_GUARDS") == "1":
+                    bad = binding.prcg_check_guards(h)
+                    if bad:
+                        raise PrcgError(binding.PRCG_ERR_CUDA,
+                                        f"{bad} guard words corrupted (out-of-bounds write)")
+            finally:
+                binding.prcg_destroy(h)
 
     def __del__(self):
         try:

@@ -32,7 +32,8 @@ EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_create_dense", "prcg_
            "prcg_time_sweeps", "prcg_solve_f32_refined", "prcg_update_faces",
            "prcg_grad_faces", "prcg_grad_csr_values",
            "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n", "prcg_error_anorm",
-           "prcg_trace_enable", "prcg_trace_get",
+           "prcg_trace_enable", "prcg_trace_get", "prcg_check_guards",
+           "prcg_inject_barrier_skip",
            "prcg_pr_solve_stencil_noalloc", "prcg_batched_create", "prcg_batched_configure",
            "prcg_batched_solve", "prcg_batched_last_ms", "prcg_batched_config",
            "prcg_batched_last_error", "prcg_batched_destroy")
@@ -96,6 +97,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.prcg_n.restype = ctypes.c_int64
     lib.prcg_error_anorm.argtypes = [vp, vp, vp, _c_double_p]
     lib.prcg_error_anorm.restype = ctypes.c_int
+    lib.prcg_inject_barrier_skip.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]
+    lib.prcg_inject_barrier_skip.restype = ctypes.c_int
+    lib.prcg_check_guards.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.prcg_check_guards.restype = ctypes.c_int
     lib.prcg_trace_enable.argtypes = [vp, ctypes.c_int]
     lib.prcg_trace_enable.restype = ctypes.c_int
     lib.prcg_trace_get.argtypes = [vp, vp, ctypes.c_int]
@@ -252,6 +257,19 @@ def prcg_last_error(ctx=None) -> str:
 
 def prcg_n(ctx) -> int:
     return int(load().prcg_n(ctx))
+
+
+def prcg_inject_barrier_skip(ctx, cta: int, barrier: int, spin_limit: int = 1 << 16):
+    """Test hook: in the next persistent solve, CTA `cta` skips grid barrier
+    `barrier`, so the solve ends with PRCG_ERR_TIMEOUT (see prcg.h)."""
+    _check(load().prcg_inject_barrier_skip(ctx, int(cta), int(barrier), int(spin_limit)), ctx)
+
+
+def prcg_check_guards(ctx) -> int:
+    """Number of corrupted guard words of the context (0 = no out-of-bounds write)."""
+    bad = ctypes.c_int64(0)
+    _check(load().prcg_check_guards(ctx, ctypes.byref(bad)), ctx)
+    return int(bad.value)
 
 
 TRACE_FIELDS = ("alpha", "beta", "nu", "nu_pred", "mu", "sigma", "gamma", "rho", "eta", "unused")

@@ -64,6 +64,27 @@ __global__ void k_csr_jacobi(const int* rp, const int* ci, const double* va, int
   }
 }
 
+// Guard bands: 256-byte blocks after every vector and partial-sum buffer,
+// filled with a signalling-NaN bit pattern (FP64 arithmetic only ever
+// produces quiet NaNs, so no computed value matches it).  An out-of-bounds
+// write by any kernel changes a guard word; prcg_check_guards counts them.
+constexpr int kGuardWords = 32;
+constexpr unsigned long long kGuardPattern = 0x7FF4DEADBEEFCAFEull;
+
+__global__ void k_guard_fill(unsigned long long* p, size_t cnt) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (size_t)gridDim.x * blockDim.x)
+    p[i] = kGuardPattern;
+}
+
+__global__ void k_guard_count(const unsigned long long* p, size_t cnt, unsigned long long* bad) {
+  unsigned long long m = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < cnt;
+       i += (size_t)gridDim.x * blockDim.x)
+    m += p[i] != kGuardPattern;
+  if (m) atomicAdd(bad, m);
+}
+
 // d_i = 1 / a_ii of a dense matrix (column-major, leading dimension lda).
 __global__ void k_dense_jacobi(const double* A, int n, int lda, double* d, int* bad) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -263,7 +284,12 @@ struct prcg_ctx {
   bool trace_on = false;         // record the scalar trace of each solve
   double* trace = nullptr;       // device, trace_cap slots x kTraceFields
   int trace_cap = 0;
-  int trace_slots = 0;           // slots written by the last solve (K + 2)
+  int trace_slots = 0;           // slots written by the last solve (K + 1)
+  std::vector<std::pair<void*, size_t>> guards;   // guard bands (pointer, 8-byte words)
+  GridBar hgb{};                 // host image of the barrier state of the next persistent launch
+  bool inject_once = false;      // hgb carries a one-shot failure injection
+  unsigned long long* dguard = nullptr;           // device counter of corrupted guard words
+  double* gscratch = nullptr;    // face-gradient scratch (variable-coefficient stencils)
   std::string err;
 };
 
@@ -288,6 +314,14 @@ int cuda_err(prcg_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_err(c, e_, #call); \
   } while (0)
 
+// Register and fill a guard band of `words` 8-byte words at p.
+int add_guard(prcg_ctx* c, void* p, size_t words) {
+  c->guards.emplace_back(p, words);
+  k_guard_fill<<<1, 256, 0, c->cs>>>(static_cast<unsigned long long*>(p), words);
+  CK(cudaGetLastError());
+  return PRCG_OK;
+}
+
 int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   c->n = n;
   c->user = (cudaStream_t)stream;
@@ -301,14 +335,19 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   CK(cudaEventCreate(&c->ev_start));
   CK(cudaEventCreate(&c->ev_init));
   CK(cudaEventCreate(&c->ev_loop));
-  // 18 n-vectors: x, b, t, d and two buffers each of r, r~, p, s, s~, w, u
+  // 18 n-vectors: x, b, t, d and two buffers each of r, r~, p, s, s~, w, u;
+  // each starts on a 256-byte boundary and is followed by a guard band that
+  // covers its rounding up to 32 entries and 32 more words
   const size_t nv = 18;
-  CK(cudaMalloc(&c->pool, nv * (size_t)n * sizeof(double)));
-  double* q = c->pool;
+  const size_t nr = ((size_t)n + 31) / 32 * 32, stride = nr + kGuardWords;
+  CK(cudaMalloc(&c->pool, (kGuardWords + nv * stride) * sizeof(double)));
+  int grc = add_guard(c, c->pool, kGuardWords);
+  double* q = c->pool + kGuardWords;
   size_t taken = 0;
   auto take = [&]() {
     double* r = q;
-    q += n;
+    if (grc == PRCG_OK) grc = add_guard(c, r + n, stride - (size_t)n);
+    q += stride;
     ++taken;
     return r;
   };
@@ -328,10 +367,13 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   }
   c->plan.pc.d = d;
   if (taken != nv) return set_err(c, PRCG_ERR_INVALID, "internal: vector pool size mismatch");
+  if (grc != PRCG_OK) return grc;
   // partial sums: kMaxGrid x (kMaxNV + 2) for the sweeps, and two epochs of
   // kMaxPersistCtas x 8 for the persistent solve's barriers (the larger)
-  CK(cudaMalloc(&c->partials, std::max((size_t)kMaxGrid * (kMaxNV + 2), (size_t)2 * kMaxPersistCtas * 8) *
-                                  sizeof(double)));
+  const size_t npart = std::max((size_t)kMaxGrid * (kMaxNV + 2), (size_t)2 * kMaxPersistCtas * 8);
+  CK(cudaMalloc(&c->partials, (npart + kGuardWords) * sizeof(double)));
+  if ((grc = add_guard(c, c->partials + npart, kGuardWords)) != PRCG_OK) return grc;
+  CK(cudaMalloc(&c->dguard, sizeof(unsigned long long)));
   CK(cudaMalloc(&c->S, sizeof(DevState)));
   CK(cudaMemset(c->S, 0, sizeof(DevState)));
   CK(cudaMallocHost(&c->hS, sizeof(DevState)));
@@ -761,8 +803,11 @@ int prcg_create_dense(prcg_ctx** out, int64_t n, const double* A, int precond, v
   op.cbw = (int)((n + ncb - 1) / ncb);
   op.ncb = (int)((n + op.cbw - 1) / op.cbw);
   const size_t na = (size_t)op.lda * (size_t)n, np = (size_t)op.ncb * (size_t)n;
-  if (cudaMalloc(&c->vpool, (na + 2 * np) * sizeof(double)) != cudaSuccess)
+  if (cudaMalloc(&c->vpool, (na + 2 * (np + kGuardWords)) * sizeof(double)) != cudaSuccess)
     return fail(set_err(c, PRCG_ERR_OOM, "matrix allocation failed"));
+  if ((rc = add_guard(c, c->vpool + na + np, kGuardWords)) != PRCG_OK) return fail(rc);
+  if ((rc = add_guard(c, c->vpool + na + 2 * np + kGuardWords, kGuardWords)) != PRCG_OK)
+    return fail(rc);
   if ((rc = wait_user(c)) != PRCG_OK) return fail(rc);
   if (cudaMemcpy2DAsync(c->vpool, (size_t)op.lda * sizeof(double), A, (size_t)n * sizeof(double),
                         (size_t)n * sizeof(double), (size_t)n, cudaMemcpyDefault,
@@ -770,7 +815,7 @@ int prcg_create_dense(prcg_ctx** out, int64_t n, const double* A, int precond, v
     return fail(cuda_err(c, cudaGetLastError(), "copy of A"));
   op.da = c->vpool;
   op.dpart[0] = c->vpool + na;
-  op.dpart[1] = c->vpool + na + np;
+  op.dpart[1] = c->vpool + na + np + kGuardWords;
   c->precond = precond;
   c->plan.pc.kind = PC_NONE;
   if (precond == PRCG_PRECOND_JACOBI) {
@@ -841,7 +886,14 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   CK(cudaEventRecord(c->ev_start, c->cs));
   bool persisted = false;
   if (persist) {
-    CK(cudaMemsetAsync(c->gb, 0, sizeof(GridBar), c->cs));
+    if (!c->inject_once) {
+      c->hgb = GridBar{};
+      c->hgb.spin_limit = kBarrierSpinLimit;
+      c->hgb.skip_cta = -1;
+      c->hgb.skip_epoch = -1;
+    }
+    c->inject_once = false;
+    CK(cudaMemcpyAsync(c->gb, &c->hgb, sizeof(GridBar), cudaMemcpyHostToDevice, c->cs));
     CK(cudaEventRecord(c->ev_init, c->cs));
     cudaError_t e = c->launch(c->plan, PH_PERSIST, variant, 0, 0, c->cs);
     if (e == cudaSuccess) {
@@ -877,7 +929,10 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   }
   const int status = h.status;
   if (status == kRunning) return set_err(c, PRCG_ERR_CUDA, "device loop ended without a status");
-  if (status < 0) return set_err(c, status, "device loop exceeded its iteration limit");
+  if (status < 0)
+    return set_err(c, status,
+                   "device loop did not finish: a bounded wait (grid barrier or copy) expired "
+                   "or the loop-body limit was reached");
   if (h.zero_rhs) CK(cudaMemsetAsync(c->plan.v.x, 0, (size_t)n * sizeof(double), c->cs));
   CK(cudaMemcpyAsync(x, c->plan.v.x, (size_t)n * sizeof(double), cudaMemcpyDefault, c->cs));
   if (residual_history) {
@@ -988,12 +1043,19 @@ int prcg_solve_f32_refined(prcg_ctx* c, const double* b, double* x, double tol, 
   if (c->plan.op.kind == OP_DENSE)
     return set_err(c, PRCG_ERR_UNSUPPORTED, "mixed precision is not built for dense matrices");
   if (!c->pool32) {
-    CK(cudaMalloc(&c->pool32, 6 * (size_t)n * sizeof(float)));
+    // six FP32 vectors, each followed by a guard band (from its rounding up
+    // to 64 entries, 64 more floats)
+    const size_t nr32 = ((size_t)n + 63) / 64 * 64, st32 = nr32 + 2 * kGuardWords;
+    CK(cudaMalloc(&c->pool32, 6 * st32 * sizeof(float)));
     CK(cudaMalloc(&c->S2, sizeof(DevState)));
     float* q = c->pool32;
+    for (int v = 0; v < 6; ++v) {
+      const int grc = add_guard(c, q + v * st32 + nr32, kGuardWords);
+      if (grc != PRCG_OK) return grc;
+    }
     Vecs32& W = c->plan.w;
-    W.r = q; W.rt = q + n; W.p = q + 2 * (size_t)n; W.s = q + 3 * (size_t)n;
-    W.d = q + 4 * (size_t)n; W.rhs = q + 5 * (size_t)n;
+    W.r = q; W.rt = q + st32; W.p = q + 2 * st32; W.s = q + 3 * st32;
+    W.d = q + 4 * st32; W.rhs = q + 5 * st32;
     c->plan.S2 = c->S2;
     if (c->plan.op.kind == OP_SELL) {
       const int nslices = (n + 31) / 32;
@@ -1126,8 +1188,11 @@ int prcg_grad_faces(prcg_ctx* c, const double* lambda, const double* x, double* 
   // lambda -> t, x -> the x buffer; the gradient is formed in the scratch s buffers
   if ((rc = copy_in(c, c->plan.v.t, lambda, n * sizeof(double))) != PRCG_OK) return rc;
   if ((rc = copy_in(c, c->plan.v.x, x, n * sizeof(double))) != PRCG_OK) return rc;
-  double* g = c->plan.v.r[1];   // r[1] .. u[1]: 7 contiguous scratch vectors, >= the faces
-  if (nf > 7 * n) return set_err(c, PRCG_ERR_INVALID, "internal: face gradient does not fit");
+  if (!c->gscratch) {
+    CK(cudaMalloc(&c->gscratch, (nf + kGuardWords) * sizeof(double)));
+    if ((rc = add_guard(c, c->gscratch + nf, kGuardWords)) != PRCG_OK) return rc;
+  }
+  double* g = c->gscratch;
   k_grad_faces<<<c->plan.sms * 8, 256, 0, c->cs>>>(dim, op.nx, op.ny, op.nz, c->plan.v.t,
                                                   c->plan.v.x, g);
   CK(cudaGetLastError());
@@ -1200,6 +1265,8 @@ int prcg_destroy(prcg_ctx* c) {
   if (c->hS) cudaFreeHost(c->hS);
   if (c->hist) cudaFree(c->hist);
   if (c->trace) cudaFree(c->trace);
+  if (c->dguard) cudaFree(c->dguard);
+  if (c->gscratch) cudaFree(c->gscratch);
   if (c->dbad) cudaFree(c->dbad);
   if (c->ev_user) cudaEventDestroy(c->ev_user);
   if (c->ev_start) cudaEventDestroy(c->ev_start);
@@ -1216,6 +1283,32 @@ const char* prcg_last_error(const prcg_ctx* c) {
 }
 
 int64_t prcg_n(const prcg_ctx* c) { return c ? (int64_t)c->n : -1; }
+
+int prcg_inject_barrier_skip(prcg_ctx* c, int cta, int barrier, int64_t spin_limit) {
+  if (!c) return set_err(nullptr, PRCG_ERR_INVALID, "ctx is NULL");
+  if (cta < 0 || barrier < 0 || spin_limit < 1024)
+    return set_err(c, PRCG_ERR_INVALID, "bad injection");
+  c->hgb = GridBar{};
+  c->hgb.spin_limit = spin_limit;
+  c->hgb.skip_cta = cta;
+  c->hgb.skip_epoch = barrier;
+  c->inject_once = true;
+  return PRCG_OK;
+}
+
+int prcg_check_guards(prcg_ctx* c, int64_t* corrupted_out) {
+  if (!c || !corrupted_out) return set_err(c, PRCG_ERR_INVALID, "NULL argument");
+  CK(cudaMemsetAsync(c->dguard, 0, sizeof(unsigned long long), c->cs));
+  for (const auto& g : c->guards)
+    k_guard_count<<<1, 256, 0, c->cs>>>(static_cast<const unsigned long long*>(g.first), g.second,
+                                        c->dguard);
+  CK(cudaGetLastError());
+  unsigned long long bad = 0;
+  CK(cudaMemcpyAsync(&bad, c->dguard, sizeof bad, cudaMemcpyDeviceToHost, c->cs));
+  CK(cudaStreamSynchronize(c->cs));
+  *corrupted_out = (int64_t)bad;
+  return PRCG_OK;
+}
 
 int prcg_trace_enable(prcg_ctx* c, int on) {
   if (!c) return set_err(nullptr, PRCG_ERR_INVALID, "ctx is NULL");

@@ -25,12 +25,18 @@ namespace prcg {
 constexpr int kPersistThreads = 1024;
 constexpr long kBarrierSpinLimit = 1L << 22;
 
-// Barrier state.  The arrival counter only grows (barrier e completes when
-// it reaches (e + 1) * gridDim.x), so no CTA ever resets it; the error flag
-// sits on its own 128-byte line.
+// Barrier state, written by the host before each launch.  The arrival
+// counter only grows (barrier e completes when it reaches (e + 1) *
+// gridDim.x), so no CTA ever resets it; the error flag sits on its own
+// 128-byte line.  spin_limit bounds every wait (polls); skip_cta / skip_epoch
+// are a failure-injection hook for tests: that CTA does not arrive at that
+// barrier, so every CTA's wait there runs out (-1: off).
 struct GridBar {
   alignas(128) unsigned count;
   alignas(128) int err;
+  long long spin_limit;
+  int skip_cta;
+  int skip_epoch;
 };
 
 constexpr int kMaxPersistCtas = 256;   // >= the SM count (one CTA per SM)
@@ -47,12 +53,15 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 // CTA after it.  Returns false once the wait has expired or another CTA has
 // given up.
 __device__ __forceinline__ bool barrier_arrive_wait(GridBar* gb, unsigned epoch) {
-  unsigned old;
-  asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&gb->count) : "memory");
+  if (!(gb->skip_cta == (int)blockIdx.x && gb->skip_epoch == (int)epoch)) {
+    unsigned old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&gb->count) : "memory");
+  }
   const unsigned target = (epoch + 1u) * gridDim.x;
+  const long limit = gb->spin_limit;
   long it = 0;
   while (ld_acquire_u32(&gb->count) < target) {
-    if ((++it & 1023) == 0 && (it > kBarrierSpinLimit || *(volatile int*)&gb->err)) {
+    if ((++it & 1023) == 0 && (it > limit || *(volatile int*)&gb->err)) {
       gb->err = 1;
       return false;
     }
