@@ -450,6 +450,13 @@ def run_batched(G, args):
         ms.append(t)
     B.close()
     best = min(ms)
+    # FP64 issue floor: every row-iteration of the batched PR-CG kernel issues
+    # 12 FP64 instructions without a preconditioner (sweep A: x, r, p and
+    # <r, r>, which is also nu; sweep B: the 5-point row and three inner
+    # products)
+    sizes = np.array([x_ * y_ for x_, y_ in zip(nx, ny)], dtype=np.float64)
+    row_iters = float((sizes * iters).sum())
+    fp64 = 12.0 * row_iters
     # plain path: the same systems, one prcg_solve each (every 4th system, scaled)
     sel = list(range(0, 512, 4))
     plain_ms = 0.0
@@ -467,6 +474,9 @@ def run_batched(G, args):
             "systems": 512, "unknowns": int(sum(x_ * y_ for x_, y_ in zip(nx, ny))),
             "iters_total": int(iters.sum()), "iters_max": int(iters.max()),
             "all_converged": bool(np.all(status == 0)), "max_true_relres": float(trr.max()),
+            "row_iterations": row_iters,
+            "fp64_frac": fp64 / (best / 1e3) / fp64_peak(),
+            "fp64_model": "12 FP64 instructions per row-iteration, peak 2 per SM per clock",
             "tuning": table,
             "plain_fp64_path": {"solves_per_s": plain_rate,
                                 "sample": "every 4th system solved alone with prcg_solve "

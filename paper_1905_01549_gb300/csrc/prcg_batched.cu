@@ -104,6 +104,10 @@ struct BatchArgs {
   int* queue;
 };
 
+// JAC: Jacobi preconditioning (a compile-time choice, so the unpreconditioned
+// kernel issues no FP64 instruction for it -- a run-time branch around an FMA
+// may be if-converted into a predicated instruction that still issues).
+template <bool JAC>
 __global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   const unsigned crank = cl.block_rank();
@@ -137,7 +141,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
     for (int i = g0; i < n; i += G) {
       const double bi = b[i];
       const double ri = bi - stencil_row(q, x, i);
-      const double rti = a.jacobi ? d * ri : ri;
+      const double rti = JAC ? d * ri : ri;
       r[i] = ri;
       rt[i] = rti;
       p[i] = rti;
@@ -190,7 +194,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
         }
       };
       cluster_sum<3>(j3, sm, slots, parity, cl, wact, [&](const double* t) {
-        scalars(nu, t[0], t[1], a.jacobi ? d * t[2] : t[2]);
+        scalars(nu, t[0], t[1], JAC ? d * t[2] : t[2]);
       });
       status = bst;
       double alpha = bc[0], beta = bc[1];
@@ -204,18 +208,18 @@ __global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
           const double rn = fma(-alpha, si, r[i]);
           r[i] = rn;
           double rtn = rn;
-          if (a.jacobi) {
+          if (JAC) {
             rtn = fma(-alpha, d * si, rt[i]);
             rt[i] = rtn;
           }
           p[i] = fma(beta, pi, rtn);
-          a2[0] = fma(rtn, rn, a2[0]);
+          if (JAC) a2[0] = fma(rtn, rn, a2[0]);   // unpreconditioned: nu_k = <r_k, r_k>
           a2[1] = fma(rn, rn, a2[1]);
         }
         cl.sync();  // p_k complete in every CTA before the product
         // sweep B: s_k = A p_k, mu_k, sigma_k, gamma_k
         double a5[5] = {a2[0], a2[1], 0.0, 0.0, 0.0};
-        const double* rtv = a.jacobi ? rt : r;
+        const double* rtv = JAC ? rt : r;
         for (int i = g0; i < n; i += G) {
           const double sn = stencil_row(q, p, i);
           s[i] = sn;
@@ -228,7 +232,7 @@ __global__ void __launch_bounds__(kMaxThreads) k_batched_pr(BatchArgs a) {
           if (t[1] <= stop2 || k == a.maxit) {
             if (threadIdx.x == 0) bst = t[1] <= stop2 ? 0 : 1;
           } else {
-            scalars(t[0], t[2], t[3], a.jacobi ? d * t[4] : t[4]);
+            scalars(JAC ? t[0] : t[1], t[2], t[3], JAC ? d * t[4] : t[4]);
           }
         });
         K = k;
@@ -336,13 +340,16 @@ cudaError_t launch_batched(prcg_batch* bt, const BatchArgs& a, cudaStream_t st) 
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_batched_pr, a);
+  return a.jacobi ? cudaLaunchKernelEx(&cfg, k_batched_pr<true>, a)
+                  : cudaLaunchKernelEx(&cfg, k_batched_pr<false>, a);
 }
 
 // Persistent grid: as many clusters as can be resident at once.
 int size_grid(prcg_batch* bt) {
+  const bool jac = bt->precond == PRCG_PRECOND_JACOBI;
+  const void* kern = jac ? (const void*)k_batched_pr<true> : (const void*)k_batched_pr<false>;
   if (bt->cluster > 8)
-    BCK(cudaFuncSetAttribute(k_batched_pr, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof cfg);
   cfg.gridDim = dim3(bt->cluster);
@@ -355,7 +362,7 @@ int size_grid(prcg_batch* bt) {
   cfg.attrs = at;
   cfg.numAttrs = 1;
   int nc = 0;
-  BCK(cudaOccupancyMaxActiveClusters(&nc, k_batched_pr, &cfg));
+  BCK(cudaOccupancyMaxActiveClusters(&nc, kern, &cfg));
   if (nc < 1) return berr(bt, PRCG_ERR_UNSUPPORTED, "cluster configuration cannot be resident");
   bt->clusters = std::min(nc, bt->nsys);
   return PRCG_OK;

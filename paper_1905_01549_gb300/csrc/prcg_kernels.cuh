@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
     acc[0] = fma(pn, sn, acc[0]);
     acc[1] = fma(rtn, sn, acc[1]);
     acc[2] = fma(stn, sn, acc[2]);
-    acc[3] = fma(rtn, rn, acc[3]);
+    if (Pc::on) acc[3] = fma(rtn, rn, acc[3]);   // unpreconditioned: nu_k = rho_k
     acc[4] = fma(rn, rn, acc[4]);
   }
   double tot[5];
@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
     S->mu = tot[0];
     S->sigma = tot[1];
     S->gamma = tot[2];
-    S->nu = tot[3];
+    S->nu = Pc::on ? tot[3] : tot[4];
     S->rho = tot[4];
     trace_pr_sums(S, k);
     if (!record_and_test(S, k, tot[4])) scalar_step_pr(S, meurant != 0);
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_b(Op op, Pc pc, Vecs V, DevState*
     const double wn = op.row(i, [&](int j) { return __ldg(rt + j); });
     V.w[0][i] = wn;
     const double rti = __ldg(rt + i), ri = __ldg(r + i);
-    acc[0] = fma(rti, ri, acc[0]);
+    if (Pc::on) acc[0] = fma(rti, ri, acc[0]);   // unpreconditioned: nu_k = <r_k, r_k>
     acc[1] = fma(rti, wn, acc[1]);
     acc[2] = fma(ri, ri, acc[2]);
   }
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(kBlock) k_gv(Op op, Pc pc, Vecs V, DevState* S
     }
     const double wn = fma(-alpha, un, wi);
     V.w[qw][i] = wn;
-    acc[0] = fma(rtn, rn, acc[0]);
+    if (Pc::on) acc[0] = fma(rtn, rn, acc[0]);   // unpreconditioned: nu_k = <r_k, r_k>
     acc[1] = fma(rtn, wn, acc[1]);
     acc[2] = fma(rn, rn, acc[2]);
   }

@@ -340,20 +340,21 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         x[i] = fma(alpha, V.p[0][i], x[i]);
         const double rn = fma(-alpha, V.s[0][i], V.r[0][i]);
         V.r[0][i] = rn;
-        a2[0] = fma(Pc::on ? pc(i) * rn : rn, rn, a2[0]);
+        if (Pc::on) a2[0] = fma(pc(i) * rn, rn, a2[0]);   // unpreconditioned: nu_k = rho_k
         a2[1] = fma(rn, rn, a2[1]);
       }
       if (!grid_sync_sum<2>(a2, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
-            ptrace(S, k, TR_NU, t[0]);
+            const double nun = Pc::on ? t[0] : t[1];
+            ptrace(S, k, TR_NU, nun);
             ptrace(S, k, TR_RHO, t[1]);
             q.status = stop_test(S, k, t[1], stop2, maxit);
             if (q.status != kRunning) return;
-            if (!finite(t[0]) || !(t[0] > 0.0)) {
+            if (!finite(nun) || !(nun > 0.0)) {
               q.status = 2;
               return;
             }
-            q.d[0] = t[0] / nu;   // beta_k
-            q.d[1] = t[0];        // nu_k
+            q.d[0] = nun / nu;   // beta_k
+            q.d[1] = nun;        // nu_k
             ptrace(S, k, TR_BETA, q.d[0]);
           })) {
         finish(S, k, -4);
@@ -417,7 +418,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
           V.rt[0][i] = rtn;
         }
         V.p[0][i] = fma(beta, pi, rtn);
-        a5[0] = fma(rtn, rn, a5[0]);
+        if (Pc::on) a5[0] = fma(rtn, rn, a5[0]);   // unpreconditioned: nu_k = rho_k
         a5[1] = fma(rn, rn, a5[1]);
       }
       if (!grid_sync(gb, epoch)) {
@@ -500,18 +501,19 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         a5[0] = fma(pn, sn, a5[0]);
         a5[1] = fma(rtn, sn, a5[1]);
         a5[2] = fma(stn, sn, a5[2]);
-        a5[3] = fma(rtn, rn, a5[3]);
+        if (Pc::on) a5[3] = fma(rtn, rn, a5[3]);   // unpreconditioned: nu_k = rho_k
         a5[4] = fma(rn, rn, a5[4]);
       }
       if (!grid_sync_sum<5>(a5, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
             ptrace(S, k, TR_MU, t[0]);
             ptrace(S, k, TR_SIGMA, t[1]);
             ptrace(S, k, TR_GAMMA, t[2]);
-            ptrace(S, k, TR_NU, t[3]);
+            const double nuk = Pc::on ? t[3] : t[4];
+            ptrace(S, k, TR_NU, nuk);
             ptrace(S, k, TR_RHO, t[4]);
             q.status = stop_test(S, k, t[4], stop2, maxit);
             if (q.status != kRunning) return;
-            pr_scalars(t[3], t[0], t[1], t[2], meurant != 0, q);
+            pr_scalars(nuk, t[0], t[1], t[2], meurant != 0, q);
             ptrace_pr_step(S, k, q);
           })) {
         finish(S, k, -4);

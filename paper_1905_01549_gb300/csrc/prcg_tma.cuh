@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe_tma(SellOp op, Pc pc, Vecs V, D
     acc[0] = fma(pn, sn, acc[0]);
     acc[1] = fma(rtn, sn, acc[1]);
     acc[2] = fma(stn, sn, acc[2]);
-    acc[3] = fma(rtn, rn, acc[3]);
+    if (Pc::on) acc[3] = fma(rtn, rn, acc[3]);   // unpreconditioned: nu_k = rho_k
     acc[4] = fma(rn, rn, acc[4]);
   });
   if (!ok) {
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe_tma(SellOp op, Pc pc, Vecs V, D
     S->mu = tot[0];
     S->sigma = tot[1];
     S->gamma = tot[2];
-    S->nu = tot[3];
+    S->nu = Pc::on ? tot[3] : tot[4];
     S->rho = tot[4];
     trace_pr_sums(S, k);
     if (!record_and_test(S, k, tot[4])) scalar_step_pr(S, meurant != 0);
