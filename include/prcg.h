@@ -143,10 +143,10 @@ int prcg_create_dense(prcg_ctx** out, int64_t n, const double* A, int precond, v
  * three) or a negative error (x untouched).  If b == 0, x is set to 0 and
  * K = 0.  The call blocks until the result is on the host.
  * Execution: for n <= 2^21 (dense contexts: n <= 4096; the environment
- * variable PRCG_PERSIST_MAX lowers the bound) HS, PR, M, pipe-PR and pipe-M
- * run as one persistent cooperative kernel (grid barriers instead of kernel
- * boundaries); larger systems, CG-CG and GV run as one CUDA graph launch
- * with a device-side while loop.
+ * variable PRCG_PERSIST_MAX lowers the bound) every variant runs as one
+ * persistent cooperative kernel (grid barriers instead of kernel
+ * boundaries); larger systems run as one CUDA graph launch with a
+ * device-side while loop.
  */
 int prcg_solve(prcg_ctx* ctx, int variant, const double* b, double* x,
                double tol, int maxit, double* residual_history,

@@ -852,9 +852,7 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   // product (one 1024-thread CTA per SM) by ~11 % at n = 10752.
   const int persist_max =
       c->plan.op.kind == OP_DENSE ? std::min(c->persist_max, kDensePersistMax) : c->persist_max;
-  const bool persist = n <= persist_max &&
-                       (variant == V_HS || variant == V_PR || variant == V_M || variant == V_PIPE ||
-                        variant == V_PIPE_M);
+  const bool persist = n <= persist_max;   // every variant has a persistent form
   bool graph = !persist && c->use_graph;
   if (graph && build_graph(c, variant) != PRCG_OK) graph = false;  // fall back to the host loop
   const int chunk = graph ? c->graphs[variant].chunk : chunk_for(c);

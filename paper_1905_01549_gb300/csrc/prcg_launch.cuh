@@ -277,6 +277,8 @@ cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, 
       if (variant == V_HS) return launch_persist<Op, Pc, V_HS>(P, 0, st);
       if (variant == V_PR || variant == V_M) return launch_persist<Op, Pc, V_PR>(P, meurant, st);
       if (variant == V_PIPE || variant == V_PIPE_M) return launch_persist<Op, Pc, V_PIPE>(P, meurant, st);
+      if (variant == V_CGCG) return launch_persist<Op, Pc, V_CGCG>(P, 0, st);
+      if (variant == V_GV) return launch_persist<Op, Pc, V_GV>(P, 0, st);
       return cudaErrorInvalidValue;
     case PH_TRUE_RES: {
       auto k = k_true_res<Op, Pc>;

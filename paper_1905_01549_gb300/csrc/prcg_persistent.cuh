@@ -7,8 +7,12 @@
 // cooperative launch of one CTA per SM; every CTA owns a fixed block of rows,
 // and the iteration's data dependencies are grid barriers:
 //   HS-CG    3 barriers per iteration (reduction, p complete, reduction)
-//   PR-CG    2 barriers per iteration (p complete, reduction)
-//   pipe-PR  1 barrier per iteration  (the reduction)
+//   PR-CG    2 barriers per iteration (p complete, reduction); M-CG alike
+//   CG-CG    2 barriers per iteration (r~ complete, reduction)
+//   pipe-PR  1 barrier per iteration  (the reduction); pipe-M-CG alike
+//   GV-CG    1 barrier per iteration  (the reduction)
+// -- the synchronisation counts of the paper's Table 1 (dense operators add
+// one barrier per product, after the in-kernel product).
 // At a reducing barrier every CTA adds all CTAs' partial sums itself, in CTA
 // order, so every CTA forms the same scalars from bitwise-identical totals,
 // takes identical control decisions and meets the same barriers.  Waiting
@@ -176,6 +180,14 @@ __device__ __forceinline__ void pr_scalars(double nu, double mu, double sigma, d
   o.d[2] = np;
 }
 
+// Scalar step of CG-CG / GV-CG (Appendix E) after the reduction of
+// nu_k, eta_k, rho_k (run by warp 0): the stopping test, beta_k =
+// nu_k / nu_{k-1}, mu_k = eta_k - (beta_k / alpha_{k-1}) nu_k, alpha_k.
+// o.d = {alpha_k, beta_k, nu_k}.
+__device__ __forceinline__ void cg_scalars(DevState* S, int k, double nu, double eta, double rho,
+                                           double nu_prev, double alpha_prev, double stop2,
+                                           int maxit, Bcast& q);
+
 // Trace writes of the persistent solve: the first thread of CTA 0 only.
 __device__ __forceinline__ void ptrace(const DevState* S, int k, int f, double v) {
   if (blockIdx.x == 0 && threadIdx.x == 0) trace(S, k, f, v);
@@ -198,6 +210,32 @@ __device__ __forceinline__ int stop_test(DevState* S, int k, double rho, double 
   return kRunning;
 }
 
+__device__ __forceinline__ void cg_scalars(DevState* S, int k, double nu, double eta, double rho,
+                                           double nu_prev, double alpha_prev, double stop2,
+                                           int maxit, Bcast& q) {
+  ptrace(S, k, TR_NU, nu);
+  ptrace(S, k, TR_ETA, eta);
+  ptrace(S, k, TR_RHO, rho);
+  q.status = stop_test(S, k, rho, stop2, maxit);
+  if (q.status != kRunning) return;
+  if (!finite(nu) || !(nu > 0.0)) {
+    q.status = 2;
+    return;
+  }
+  const double beta = nu / nu_prev;
+  const double mu = eta - (beta / alpha_prev) * nu;
+  if (!finite(mu) || !(mu > 0.0)) {
+    q.status = 2;
+    return;
+  }
+  q.d[0] = nu / mu;
+  q.d[1] = beta;
+  q.d[2] = nu;
+  ptrace(S, k, TR_BETA, beta);
+  ptrace(S, k, TR_MU, mu);
+  ptrace(S, k + 1, TR_ALPHA, q.d[0]);
+}
+
 __device__ __forceinline__ void finish(DevState* S, int k, int status) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     S->k = k;
@@ -208,20 +246,32 @@ __device__ __forceinline__ void finish(DevState* S, int k, int status) {
 
 constexpr int kZeroRhs = -101;   // internal: b == 0
 
+// The Jacobi vector of a preconditioner, or NULL (GV-CG's dense product of
+// M^{-1} w).
+template <class Pc>
+__device__ __forceinline__ const double* pc_vector(const Pc&) {
+  return nullptr;
+}
+__device__ __forceinline__ const double* pc_vector(const PcVec& p) { return p.d; }
+
 // Dense operators: every warp of the grid forms its units of the product
 // with v0 (and v1), then a barrier makes the partials visible to the row
 // loop that follows.  Other operators gather inside the row loop: no-op.
 template <class Op>
 __device__ __forceinline__ bool persist_product(const Op& op, const double* v0, const double* v1,
-                                                GridBar* gb, unsigned& epoch) {
+                                                GridBar* gb, unsigned& epoch,
+                                                const double* scale = nullptr) {
   if constexpr (IsDense<Op>::value) {
     DenseSrc s0, s1;
     s0.a = v0;
+    s0.scale = scale;
     s1.a = v1;
     const int gw = (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5));
     const int nw = (int)(gridDim.x * (blockDim.x >> 5));
     if (v1)
       dense_units<2, DS_PLAIN>(op, s0, s1, gw, nw);
+    else if (scale)
+      dense_units<1, DS_SCALE>(op, s0, s1, gw, nw);
     else
       dense_units<1, DS_PLAIN>(op, s0, s1, gw, nw);
     return grid_sync(gb, epoch);
@@ -231,7 +281,7 @@ __device__ __forceinline__ bool persist_product(const Op& op, const double* v0, 
 }
 
 // One persistent solve.  VARIANT: V_HS, V_PR (meurant -> M-CG), V_PIPE
-// (meurant -> pipe-PR-M-CG).
+// (meurant -> pipe-PR-M-CG), V_CGCG, V_GV.
 template <class Op, class Pc, int VARIANT>
 __global__ void __launch_bounds__(kPersistThreads, 1)
     k_persist(Op op, Pc pc, Vecs V, DevState* S, double* partials, GridBar* gb, int meurant) {
@@ -300,7 +350,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       const double s = op.row(i, [&](int j) { return __ldcg(p0 + j); });
       const double st = Pc::on ? pc(i) * s : s;
       V.s[0][i] = s;
-      if (VARIANT == V_PIPE && Pc::on) V.st[0][i] = st;
+      if ((VARIANT == V_PIPE || VARIANT == V_GV) && Pc::on) V.st[0][i] = st;
+      if (VARIANT == V_CGCG || VARIANT == V_GV) V.w[0][i] = s;   // w_0 = A r~_0 = s_0 (p_0 = r~_0)
+      if (VARIANT == V_GV) V.u[0][i] = 0.0;   // multiplied by beta_0 = 0 in the first sweep
       const double rt = Pc::on ? V.rt[0][i] : V.r[0][i];
       b3[0] = fma(p0[i], s, b3[0]);
       b3[1] = fma(rt, s, b3[1]);
@@ -310,7 +362,8 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
           ptrace(S, 0, TR_MU, t[0]);
           ptrace(S, 0, TR_SIGMA, t[1]);
           ptrace(S, 0, TR_GAMMA, t[2]);
-          if (VARIANT == V_HS) {
+          if (VARIANT == V_HS || VARIANT == V_CGCG || VARIANT == V_GV) {
+            // alpha_0; CG-CG / GV-CG start with beta_0 = 0 (o.d[1] stays 0)
             if (!finite(nu) || !finite(t[0]) || !(t[0] > 0.0) || nu < 0.0) {
               q.status = 2;
             } else {
@@ -459,7 +512,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       }
       alpha = o.d[0];
       beta = o.d[1];
-    } else {
+    } else if (VARIANT == V_PIPE) {
       // pipe: u_{k-1}, w_{k-1} from buffer qr, updates of iteration k to qw
       const int qr = (k - 1) & 1, qw = k & 1;
       const double* rt_o = Pc::on ? V.rt[qr] : V.r[qr];
@@ -525,6 +578,106 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
       }
       alpha = o.d[0];
       beta = o.d[1];
+    } else if (VARIANT == V_CGCG) {
+      // A: finish iteration k-1 (p, s with beta_{k-1}), then x_k, r_k and
+      // r~_k = M^{-1} r_k (row-local)
+      PRCG_OWN_ROWS(i, rb) {
+        const double rti = Pc::on ? V.rt[0][i] : V.r[0][i];
+        const double pn = fma(beta, V.p[0][i], rti);
+        const double sn = fma(beta, V.s[0][i], V.w[0][i]);
+        V.p[0][i] = pn;
+        V.s[0][i] = sn;
+        x[i] = fma(alpha, pn, x[i]);
+        const double rn = fma(-alpha, sn, V.r[0][i]);
+        V.r[0][i] = rn;
+        if (Pc::on) V.rt[0][i] = pc(i) * rn;
+      }
+      if (!grid_sync(gb, epoch)) {
+        finish(S, k, -4);
+        return;
+      }
+      // B: w_k = A r~_k; nu_k, eta_k = <r~_k, w_k>, rho_k
+      const double* rtv = Pc::on ? V.rt[0] : V.r[0];
+      if (!persist_product(op, rtv, nullptr, gb, epoch)) {
+        finish(S, k, -4);
+        return;
+      }
+      double a3[3] = {0.0, 0.0, 0.0};
+      PRCG_OWN_ROWS(i, rb) {
+        const double wn = op.row(i, [&](int j) { return __ldcg(rtv + j); });
+        V.w[0][i] = wn;
+        const double rti = rtv[i], ri = V.r[0][i];
+        if (Pc::on) a3[0] = fma(rti, ri, a3[0]);   // unpreconditioned: nu_k = rho_k
+        a3[1] = fma(rti, wn, a3[1]);
+        a3[2] = fma(ri, ri, a3[2]);
+      }
+      if (!grid_sync_sum<3>(a3, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
+            cg_scalars(S, k, Pc::on ? t[0] : t[2], t[1], t[2], nu, alpha, stop2, maxit, q);
+          })) {
+        finish(S, k, -4);
+        return;
+      }
+      if (o.status != kRunning) {
+        finish(S, k, o.status);
+        return;
+      }
+      alpha = o.d[0];
+      beta = o.d[1];
+      nu = o.d[2];
+    } else {
+      // GV-CG: t_{k-1} = A M^{-1} w_{k-1} from buffer qr, the updates that
+      // finish iteration k-1 (p, s, s~, u with beta_{k-1}), those of iteration
+      // k (x_k, r_k, r~_k, w_k to buffer qw) and nu_k, eta_k, rho_k
+      const int qr = (k - 1) & 1, qw = k & 1;
+      const double* w_o = V.w[qr];
+      if (!persist_product(op, w_o, nullptr, gb, epoch, pc_vector(pc))) {
+        finish(S, k, -4);
+        return;
+      }
+      double a3[3] = {0.0, 0.0, 0.0};
+      PRCG_OWN_ROWS(i, rb) {
+        const double t = op.row(i, [&](int j) {
+          const double wj = __ldcg(w_o + j);
+          return Pc::on ? pc(j) * wj : wj;
+        });
+        const double wi = w_o[i];
+        const double rti = Pc::on ? V.rt[0][i] : V.r[0][i];
+        const double pn = fma(beta, V.p[0][i], rti);
+        const double sn = fma(beta, V.s[0][i], wi);
+        const double un = fma(beta, V.u[0][i], t);
+        double stn = sn;
+        if (Pc::on) stn = fma(beta, V.st[0][i], pc(i) * wi);
+        V.p[0][i] = pn;
+        V.s[0][i] = sn;
+        V.u[0][i] = un;
+        x[i] = fma(alpha, pn, x[i]);
+        const double rn = fma(-alpha, sn, V.r[0][i]);
+        V.r[0][i] = rn;
+        double rtn = rn;
+        if (Pc::on) {
+          V.st[0][i] = stn;
+          rtn = fma(-alpha, stn, rti);
+          V.rt[0][i] = rtn;
+        }
+        const double wn = fma(-alpha, un, wi);
+        V.w[qw][i] = wn;
+        if (Pc::on) a3[0] = fma(rtn, rn, a3[0]);   // unpreconditioned: nu_k = rho_k
+        a3[1] = fma(rtn, wn, a3[1]);
+        a3[2] = fma(rn, rn, a3[2]);
+      }
+      if (!grid_sync_sum<3>(a3, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
+            cg_scalars(S, k, Pc::on ? t[0] : t[2], t[1], t[2], nu, alpha, stop2, maxit, q);
+          })) {
+        finish(S, k, -4);
+        return;
+      }
+      if (o.status != kRunning) {
+        finish(S, k, o.status);
+        return;
+      }
+      alpha = o.d[0];
+      beta = o.d[1];
+      nu = o.d[2];
     }
   }
   finish(S, maxit, 1);

@@ -70,7 +70,7 @@ def test_dense_first_20_iterations(G, name, path, monkeypatch):
             assert rel(res.x.cpu().numpy(), ref.x) <= bar, (v, rel(res.x.cpu().numpy(), ref.x), bar)
             from paper_1905_01549_gb300 import binding
             launches = binding.prcg_last_launches(S.handle)
-            persistent = path == "persistent" and v not in ("cgcg", "gv")
+            persistent = path == "persistent"
             assert (launches == 1) == persistent, (v, launches)
 
 

@@ -27,7 +27,8 @@ def G():
     return G
 
 
-@pytest.mark.parametrize("variant,barrier", [("pr", 0), ("pr", 7), ("hs", 5), ("pipe_pr", 12)])
+@pytest.mark.parametrize("variant,barrier", [("pr", 0), ("pr", 7), ("hs", 5), ("pipe_pr", 12),
+                                             ("cgcg", 6), ("gv", 9)])
 def test_skipped_barrier_times_out_and_context_recovers(G, variant, barrier):
     import torch
     from paper_1905_01549_gb300 import binding

@@ -227,7 +227,7 @@ def test_persistent_and_graph_paths_match_oracle(G, torch_mod, name, op, precond
         if mode == "graph":
             monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
         with make_solver(G, prob, op, precond) as S:
-            for variant in ("hs", "pr", "pipe_pr", "m", "pipe_m"):
+            for variant in GPU_VARIANTS:
                 res = S.solve(b, variant=variant, tol=0.0, maxit=20)
                 ref = O.solve(variant, A, prob.b, d=d, tol=0.0, maxit=20)
                 assert rel(res.x.cpu().numpy(), ref.x) <= ITER_TOL, (mode, variant)
