@@ -5,9 +5,12 @@
 // every slice start is a multiple of 32 entries, so both byte offsets are
 // 128-byte aligned and every size is a multiple of 16 bytes).  One thread
 // moves a whole tile's entries into shared memory with two cp.async.bulk
-// copies completing on an mbarrier; while the CTA computes tile m, tile m+1
-// is in flight (two stages).  The rows' own vector entries and the gathered
-// columns still go through ordinary loads.  Every wait on an mbarrier is
+// copies completing on a "full" mbarrier; while the CTA computes tile m,
+// tile m+1 is in flight (two stages).  Warps release a stage on its "empty"
+// mbarrier and the copying thread refills it once all have, so warps never
+// meet at a CTA-wide barrier between tiles.  The rows' own vector entries and
+// the gathered columns still go through ordinary loads.  Every wait on an
+// mbarrier is
 // bounded: after kTmaSpinLimit polls the kernel records PRCG_ERR_TIMEOUT in
 // the scalar block, waits (bounded) for its copies in flight and returns.
 #pragma once
@@ -24,7 +27,8 @@ constexpr long kTmaSpinLimit = 1L << 24;
 struct __align__(128) TmaSmem {
   int col[kTmaStages][kTmaCap];
   double val[kTmaStages][kTmaCap];
-  unsigned long long bar[kTmaStages];
+  unsigned long long bar[kTmaStages];     // "full": the stage's copies have landed
+  unsigned long long empty[kTmaStages];   // every warp is done with the stage
   int failed;
 };
 
@@ -32,8 +36,13 @@ __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ void mbar_init(unsigned long long* bar) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count = 1) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
 __device__ __forceinline__ void fence_barrier_init() {
@@ -93,14 +102,21 @@ __device__ __forceinline__ void tma_issue(TmaSmem& sm, const SellOp& op, int til
 // Run `row(i, visit)` for every row of this CTA's tiles with the tile's
 // entries staged in shared memory; visit(f) calls f(j, a_ij) for the row's
 // entries in stored order (padding entries included, as the SELL sweep does).
-// Returns false if a wait timed out (the caller reports the error).
+// Each warp waits for its tile's "full" barrier itself and, when done,
+// arrives on the stage's "empty" barrier; thread 0 refills a stage once
+// every warp has released it, so no warp waits for the slowest one between
+// tiles.  Returns false if a wait timed out (the caller reports the error).
 template <class RowFn>
 __device__ __forceinline__ bool sell_tma_sweep(TmaSmem& sm, const SellOp& op, RowFn&& row) {
   const int ntiles = (op.n + kTmaRows - 1) / kTmaRows;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  volatile int* failed = &sm.failed;
   int issued[kTmaStages] = {0, 0};     // thread 0's bookkeeping of copies per stage
   if (tid == 0) {
-    for (int q = 0; q < kTmaStages; ++q) mbar_init(&sm.bar[q]);
+    for (int q = 0; q < kTmaStages; ++q) {
+      mbar_init(&sm.bar[q]);
+      mbar_init(&sm.empty[q], blockDim.x >> 5);
+    }
     sm.failed = 0;
     fence_barrier_init();
   }
@@ -114,15 +130,18 @@ __device__ __forceinline__ bool sell_tma_sweep(TmaSmem& sm, const SellOp& op, Ro
       }
     }
   }
-  int consumed = 0;   // tiles of this CTA whose stage phase has been observed
+  int consumed = 0;   // tiles whose "full" phase thread 0 has observed
   int m = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++m) {
     const int stage = m % kTmaStages;
     const unsigned parity = (unsigned)((m / kTmaStages) & 1);
-    if (!mbar_wait_bounded(&sm.bar[stage], parity)) sm.failed = 1;
-    __syncthreads();
-    if (sm.failed) break;
-    ++consumed;
+    const bool landed = mbar_wait_bounded(&sm.bar[stage], parity);
+    const int stop = __shfl_sync(0xffffffffu, lane == 0 ? *failed : 0, 0);
+    if (!__all_sync(0xffffffffu, landed) || stop) {   // warp-uniform decision
+      if (lane == 0) *failed = 1;
+      break;
+    }
+    if (tid == 0) ++consumed;
     const int i = t * kTmaRows + tid;
     if (i < op.n) {
       const int sl = i >> 5;
@@ -135,16 +154,22 @@ __device__ __forceinline__ bool sell_tma_sweep(TmaSmem& sm, const SellOp& op, Ro
         for (int e = 0; e < L; ++e) f(cs[off + 32 * e], vs[off + 32 * e]);
       });
     }
-    __syncthreads();   // every thread is done with this stage
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&sm.empty[stage]);   // this warp is done with the stage
     if (tid == 0) {
       const int tn = t + kTmaStages * gridDim.x;
       if (tn < ntiles) {
-        fence_proxy_async();
-        tma_issue(sm, op, tn, stage);
-        ++issued[stage];
+        if (mbar_wait_bounded(&sm.empty[stage], parity)) {
+          fence_proxy_async();
+          tma_issue(sm, op, tn, stage);
+          ++issued[stage];
+        } else {
+          *failed = 1;
+        }
       }
     }
   }
+  __syncthreads();
   const bool ok = sm.failed == 0;
   if (!ok && tid == 0) {
     // drain (bounded) every copy issued but not yet observed, before exit
