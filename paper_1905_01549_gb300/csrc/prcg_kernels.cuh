@@ -129,12 +129,34 @@ __global__ void __launch_bounds__(kBlock) k_hs_a(Op op, Pc pc, Vecs V, DevState*
   double* __restrict__ r = V.r[0];
   const double* __restrict__ s = V.s[0];
   double* __restrict__ x = V.x;
-  PRCG_ROWS(i, op.n) {
-    x[i] = fma(alpha, __ldg(p + i), x[i]);
-    const double rn = fma(-alpha, __ldg(s + i), r[i]);
-    r[i] = rn;
+  constexpr bool kNuDot = Pc::on && !std::is_same<Pc, PcScalar>::value;
+  auto update = [&](double pi, double si, double& xi, double& ri, double di) {
+    xi = fma(alpha, pi, xi);
+    const double rn = fma(-alpha, si, ri);
+    ri = rn;
     acc[1] = fma(rn, rn, acc[1]);
-    if (Pc::on && !std::is_same<Pc, PcScalar>::value) acc[0] = fma(pc(i) * rn, rn, acc[0]);
+    if (kNuDot) acc[0] = fma(di * rn, rn, acc[0]);
+  };
+  // two rows per thread with 16-byte accesses (as in k_pr_a)
+  const int n = op.n, npair = n >> 1;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < npair; j += gridDim.x * blockDim.x) {
+    const int i = 2 * j;
+    const double2 p2 = __ldg(reinterpret_cast<const double2*>(p + i));
+    const double2 s2 = __ldg(reinterpret_cast<const double2*>(s + i));
+    double2 x2 = *reinterpret_cast<const double2*>(x + i);
+    double2 r2 = *reinterpret_cast<const double2*>(r + i);
+    const double2 d2 = kNuDot ? pc_pair(pc, i) : make_double2(1.0, 1.0);
+    update(p2.x, s2.x, x2.x, r2.x, d2.x);
+    update(p2.y, s2.y, x2.y, r2.y, d2.y);
+    *reinterpret_cast<double2*>(x + i) = x2;
+    *reinterpret_cast<double2*>(r + i) = r2;
+  }
+  if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    const int i = n - 1;
+    double xi = x[i], ri = r[i];
+    update(__ldg(p + i), __ldg(s + i), xi, ri, kNuDot ? pc(i) : 1.0);
+    x[i] = xi;
+    r[i] = ri;
   }
   double tot[2];
   if (grid_sum<2>(acc, partials, S, tot) && threadIdx.x == 0) {
@@ -165,10 +187,21 @@ __global__ void __launch_bounds__(kBlock) k_hs_b(Op op, Pc pc, Vecs V, DevState*
   const double beta = __ldcg(&S->beta);
   double* __restrict__ p = V.p[0];
   const double* __restrict__ r = V.r[0];
-  PRCG_ROWS(i, op.n) {
+  // two rows per thread with 16-byte accesses (as in k_pr_a)
+  const int n = op.n, npair = n >> 1;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < npair; j += gridDim.x * blockDim.x) {
+    const int i = 2 * j;
+    const double2 r2 = __ldg(reinterpret_cast<const double2*>(r + i));
+    const double2 d2 = Pc::on ? pc_pair(pc, i) : make_double2(1.0, 1.0);
+    double2 p2 = *reinterpret_cast<const double2*>(p + i);
+    p2.x = fma(beta, p2.x, Pc::on ? d2.x * r2.x : r2.x);
+    p2.y = fma(beta, p2.y, Pc::on ? d2.y * r2.y : r2.y);
+    *reinterpret_cast<double2*>(p + i) = p2;
+  }
+  if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    const int i = n - 1;
     const double ri = __ldg(r + i);
-    const double rt = Pc::on ? pc(i) * ri : ri;
-    p[i] = fma(beta, p[i], rt);
+    p[i] = fma(beta, p[i], Pc::on ? pc(i) * ri : ri);
   }
 }
 
@@ -215,19 +248,46 @@ __global__ void __launch_bounds__(kBlock) k_pr_a(Op op, Pc pc, Vecs V, DevState*
   double* __restrict__ p = V.p[0];
   const double* __restrict__ s = V.s[0];
   double acc[2] = {0.0, 0.0};
-  PRCG_ROWS(i, op.n) {
-    const double si = __ldg(s + i);
-    x[i] = fma(alpha, p[i], x[i]);
-    const double rn = fma(-alpha, si, r[i]);
-    r[i] = rn;
+  // the update of one row from its old values; returns rtn and writes x, r, p
+  auto update = [&](double si, double pi, double& xi, double& ri, double& rti, double di) {
+    xi = fma(alpha, pi, xi);
+    const double rn = fma(-alpha, si, ri);
+    ri = rn;
     double rtn = rn;
     if (Pc::on) {
-      rtn = fma(-alpha, pc(i) * si, rt[i]);
-      rt[i] = rtn;
+      rtn = fma(-alpha, di * si, rti);
+      rti = rtn;
       acc[0] = fma(rtn, rn, acc[0]);
     }
-    p[i] = fma(beta, p[i], rtn);
     acc[1] = fma(rn, rn, acc[1]);
+    return fma(beta, pi, rtn);   // p_k
+  };
+  // two rows per thread: 16-byte loads and stores halve the memory requests
+  // of this streaming sweep (vectors start on 256-byte boundaries)
+  const int n = op.n, npair = n >> 1;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < npair; j += gridDim.x * blockDim.x) {
+    const int i = 2 * j;
+    const double2 s2 = __ldg(reinterpret_cast<const double2*>(s + i));
+    const double2 p2 = *reinterpret_cast<const double2*>(p + i);
+    double2 x2 = *reinterpret_cast<const double2*>(x + i);
+    double2 r2 = *reinterpret_cast<const double2*>(r + i);
+    double2 rt2 = Pc::on ? *reinterpret_cast<const double2*>(rt + i) : make_double2(0.0, 0.0);
+    const double2 d2 = pc_pair(pc, i);
+    double2 pn;
+    pn.x = update(s2.x, p2.x, x2.x, r2.x, rt2.x, d2.x);
+    pn.y = update(s2.y, p2.y, x2.y, r2.y, rt2.y, d2.y);
+    *reinterpret_cast<double2*>(x + i) = x2;
+    *reinterpret_cast<double2*>(r + i) = r2;
+    if (Pc::on) *reinterpret_cast<double2*>(rt + i) = rt2;
+    *reinterpret_cast<double2*>(p + i) = pn;
+  }
+  if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    const int i = n - 1;
+    double xi = x[i], ri = r[i], rti = Pc::on ? rt[i] : 0.0;
+    p[i] = update(__ldg(s + i), p[i], xi, ri, rti, Pc::on ? pc(i) : 1.0);
+    x[i] = xi;
+    r[i] = ri;
+    if (Pc::on) rt[i] = rti;
   }
   __shared__ double sm[2 * 32];
   block_sum<2>(acc, sm);

@@ -290,6 +290,13 @@ struct DenseOp {
   }
 };
 
+// The preconditioner's d_i, d_{i+1} (i even; vectors start on 256-byte
+// boundaries, so the pair is one 16-byte load for a Jacobi vector).
+template <class Pc>
+__device__ __forceinline__ double2 pc_pair(const Pc& pc, int i) {
+  return make_double2(pc(i), pc(i + 1));
+}
+
 template <class Op>
 struct IsDense : std::false_type {};
 template <>
@@ -313,5 +320,9 @@ struct PcVec {
   explicit PcVec(const PcDesc& p) : d(p.d) {}
   __device__ __forceinline__ double operator()(int i) const { return __ldg(d + i); }
 };
+
+__device__ __forceinline__ double2 pc_pair(const PcVec& pc, int i) {
+  return __ldg(reinterpret_cast<const double2*>(pc.d + i));
+}
 
 }  // namespace prcg
