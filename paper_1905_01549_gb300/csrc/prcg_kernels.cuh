@@ -624,20 +624,48 @@ __global__ void __launch_bounds__(kBlock) k_mx_pr_a(Op op, Pc pc, Vecs32 W, DevS
   const float af = (float)__ldcg(&S->alpha);
   const float bf = (float)__ldcg(&S->beta);
   KahanF nu, rr;
-  PRCG_ROWS(i, op.n) {
-    const float si = W.s[i];
-    const float pi = W.p[i];
-    W.d[i] = fmaf(af, pi, W.d[i]);
-    const float rn = fmaf(-af, si, W.r[i]);
-    W.r[i] = rn;
+  // the update of one row; returns p_k and writes d, r, r~
+  auto update = [&](float si, float pi, float& di, float& ri, float& rti, float dd) {
+    di = fmaf(af, pi, di);
+    const float rn = fmaf(-af, si, ri);
+    ri = rn;
     float rtn = rn;
     if (Pc::on) {
-      rtn = fmaf(-af, (float)pc(i) * si, W.rt[i]);
-      W.rt[i] = rtn;
+      rtn = fmaf(-af, dd * si, rti);
+      rti = rtn;
     }
-    W.p[i] = fmaf(bf, pi, rtn);
     nu.add(rtn * rn);
     rr.add(rn * rn);
+    return fmaf(bf, pi, rtn);
+  };
+  // four rows per thread with 16-byte accesses (FP32 vectors start on
+  // 256-byte boundaries); the last CTA takes the n mod 4 remaining rows
+  const int n = op.n, nq = n >> 2;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nq; j += gridDim.x * blockDim.x) {
+    const int i = 4 * j;
+    const float4 s4 = *reinterpret_cast<const float4*>(W.s + i);
+    const float4 p4 = *reinterpret_cast<const float4*>(W.p + i);
+    float4 d4 = *reinterpret_cast<const float4*>(W.d + i);
+    float4 r4 = *reinterpret_cast<const float4*>(W.r + i);
+    float4 rt4 = Pc::on ? *reinterpret_cast<const float4*>(W.rt + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 c4 = pc_quad32(pc, i);
+    float4 pn;
+    pn.x = update(s4.x, p4.x, d4.x, r4.x, rt4.x, c4.x);
+    pn.y = update(s4.y, p4.y, d4.y, r4.y, rt4.y, c4.y);
+    pn.z = update(s4.z, p4.z, d4.z, r4.z, rt4.z, c4.z);
+    pn.w = update(s4.w, p4.w, d4.w, r4.w, rt4.w, c4.w);
+    *reinterpret_cast<float4*>(W.d + i) = d4;
+    *reinterpret_cast<float4*>(W.r + i) = r4;
+    if (Pc::on) *reinterpret_cast<float4*>(W.rt + i) = rt4;
+    *reinterpret_cast<float4*>(W.p + i) = pn;
+  }
+  if (blockIdx.x == gridDim.x - 1 && (int)threadIdx.x < n - 4 * nq) {
+    const int i = 4 * nq + threadIdx.x;
+    float di = W.d[i], ri = W.r[i], rti = Pc::on ? W.rt[i] : 0.f;
+    W.p[i] = update(W.s[i], W.p[i], di, ri, rti, Pc::on ? (float)pc(i) : 1.f);
+    W.d[i] = di;
+    W.r[i] = ri;
+    if (Pc::on) W.rt[i] = rti;
   }
   double acc[2] = {Pc::on ? nu.value() : rr.value(), rr.value()};
   __shared__ double sm[2 * 32];
@@ -658,12 +686,35 @@ __global__ void __launch_bounds__(kBlock) k_mx_pr_b(Op op, Pc pc, Vecs32 W, DevS
   KahanF mu, sg, ga;
   const float* __restrict__ p = W.p;
   const float* __restrict__ rt = Pc::on ? W.rt : W.r;
-  PRCG_ROWS(i, op.n) {
-    const float sn = op.row32(i, [&](int j) { return __ldg(p + j); });
+  auto gather = [&](int j) { return __ldg(p + j); };
+  auto sums = [&](float sn, float pi, float rti, float dd) {
+    mu.add(pi * sn);
+    sg.add(rti * sn);
+    ga.add((Pc::on ? dd * sn : sn) * sn);
+  };
+  // four rows per thread: the rows' own p, r~ and s move with 16-byte accesses
+  const int n = op.n, nq = n >> 2;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nq; j += gridDim.x * blockDim.x) {
+    const int i = 4 * j;
+    float4 s4;
+    s4.x = op.row32(i, gather);
+    s4.y = op.row32(i + 1, gather);
+    s4.z = op.row32(i + 2, gather);
+    s4.w = op.row32(i + 3, gather);
+    *reinterpret_cast<float4*>(W.s + i) = s4;
+    const float4 p4 = __ldg(reinterpret_cast<const float4*>(p + i));
+    const float4 rt4 = __ldg(reinterpret_cast<const float4*>(rt + i));
+    const float4 c4 = pc_quad32(pc, i);
+    sums(s4.x, p4.x, rt4.x, c4.x);
+    sums(s4.y, p4.y, rt4.y, c4.y);
+    sums(s4.z, p4.z, rt4.z, c4.z);
+    sums(s4.w, p4.w, rt4.w, c4.w);
+  }
+  if (blockIdx.x == gridDim.x - 1 && (int)threadIdx.x < n - 4 * nq) {
+    const int i = 4 * nq + threadIdx.x;
+    const float sn = op.row32(i, gather);
     W.s[i] = sn;
-    mu.add(__ldg(p + i) * sn);
-    sg.add(__ldg(rt + i) * sn);
-    ga.add((Pc::on ? (float)pc(i) * sn : sn) * sn);
+    sums(sn, __ldg(p + i), __ldg(rt + i), Pc::on ? (float)pc(i) : 1.f);
   }
   double acc[3] = {mu.value(), sg.value(), ga.value()};
   double tot[3];

@@ -297,6 +297,13 @@ __device__ __forceinline__ double2 pc_pair(const Pc& pc, int i) {
   return make_double2(pc(i), pc(i + 1));
 }
 
+// The same for four rows (i a multiple of 4), rounded to FP32 for the
+// mixed-precision inner solve.
+template <class Pc>
+__device__ __forceinline__ float4 pc_quad32(const Pc& pc, int i) {
+  return make_float4((float)pc(i), (float)pc(i + 1), (float)pc(i + 2), (float)pc(i + 3));
+}
+
 template <class Op>
 struct IsDense : std::false_type {};
 template <>
@@ -323,6 +330,12 @@ struct PcVec {
 
 __device__ __forceinline__ double2 pc_pair(const PcVec& pc, int i) {
   return __ldg(reinterpret_cast<const double2*>(pc.d + i));
+}
+
+__device__ __forceinline__ float4 pc_quad32(const PcVec& pc, int i) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(pc.d + i));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(pc.d + i + 2));
+  return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
 }
 
 }  // namespace prcg
