@@ -696,11 +696,7 @@ __global__ void __launch_bounds__(kBlock) k_mx_pr_b(Op op, Pc pc, Vecs32 W, DevS
   const int n = op.n, nq = n >> 2;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < nq; j += gridDim.x * blockDim.x) {
     const int i = 4 * j;
-    float4 s4;
-    s4.x = op.row32(i, gather);
-    s4.y = op.row32(i + 1, gather);
-    s4.z = op.row32(i + 2, gather);
-    s4.w = op.row32(i + 3, gather);
+    const float4 s4 = rows32x4(op, i, p);
     *reinterpret_cast<float4*>(W.s + i) = s4;
     const float4 p4 = __ldg(reinterpret_cast<const float4*>(p + i));
     const float4 rt4 = __ldg(reinterpret_cast<const float4*>(rt + i));

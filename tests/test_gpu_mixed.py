@@ -21,7 +21,8 @@ def G():
     return G
 
 
-@pytest.mark.parametrize("name", ["poisson2d_64", "poisson3d_ragged", "varcoef3d_ragged"])
+@pytest.mark.parametrize("name", ["poisson2d_64", "poisson3d_ragged", "varcoef3d_ragged",
+                                  "poisson3d_nx24"])
 @pytest.mark.parametrize("op", ["csr", "stencil"])
 @pytest.mark.parametrize("precond", ["none", "jacobi"])
 def test_mixed_reaches_fp64_tolerance(G, name, op, precond):
