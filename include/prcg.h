@@ -66,8 +66,10 @@ enum prcg_status {
     PRCG_ERR_INVALID = -1,     /* bad argument                                  */
     PRCG_ERR_CUDA = -2,        /* a CUDA call failed                            */
     PRCG_ERR_OOM = -3,         /* device allocation failed                      */
-    PRCG_ERR_TIMEOUT = -4,     /* the device loop ran more bodies than maxit
-                                  allows (internal safety limit)                */
+    PRCG_ERR_TIMEOUT = -4,     /* a bounded device wait expired (a grid
+                                  barrier of the persistent kernel or a TMA
+                                  copy), or the device loop ran more bodies
+                                  than maxit allows (internal safety limit)  */
     PRCG_ERR_UNSUPPORTED = -5  /* variant / operator combination not built      */
 };
 
@@ -223,16 +225,21 @@ int prcg_last_timing(const prcg_ctx* ctx, float* init_ms, float* loop_ms, int* i
  * unspecified state (the next prcg_solve copies its own b and x_0 in).
  *   ms_per_sweep  float[3]: HS: sweeps A (x, r), B (p), C (s = A p);
  *                 PR / M: A (x, r, r~, p), B (s = A p and the inner products);
- *                 pipe-PR / pipe-M: the single sweep
+ *                 CG-CG: A (p, s, x, r, r~), B (w = A r~ and the inner
+ *                 products); pipe-PR / pipe-M / GV: the single sweep.  For a
+ *                 dense context a product sweep's time includes its product
+ *                 kernel.  The sweeps are those of the graph path.
  *   nsweeps       receives the number of sweeps written (3, 2 or 1)
  */
 int prcg_time_sweeps(prcg_ctx* ctx, int variant, int reps, float* ms_per_sweep, int* nsweeps);
 
 /*
  * prcg_last_launches -- number of this library's kernels the last
- * prcg_solve launched (initialisation sweeps, iteration sweeps including the
- * no-op sweeps after convergence within the last loop body, loop-control
- * kernels, and the optional true-residual sweep).
+ * prcg_solve launched: 1 for a persistent solve (plus the optional
+ * true-residual sweep); otherwise the initialisation sweeps, the iteration
+ * sweeps including the no-op sweeps after convergence within the last loop
+ * body, the loop-control kernels, a dense context's product kernels, and
+ * the optional true-residual sweep.
  */
 int prcg_last_launches(const prcg_ctx* ctx, int64_t* kernels);
 
@@ -286,8 +293,9 @@ int prcg_check_guards(prcg_ctx* ctx, int64_t* corrupted_out);
  * sigma_k, gamma_k, rho_k = <r_k, r_k>, eta_k (CG-CG, GV-CG), unused.
  * Slot 0 holds initialize()'s nu_0, mu_0, sigma_0, gamma_0, rho_0.  Fields a
  * variant does not form are NaN, and so are those of slot K that follow the
- * stopping test (beta_K, mu_K of HS-CG, for instance).  The paper has no counterpart: this exposes the
- * quantities its analysis (Section 3) reasons about, for tests and studies.
+ * stopping test (beta_K, mu_K of HS-CG, for instance).  The paper has no
+ * counterpart: this exposes the quantities its analysis (Section 3) reasons
+ * about, for tests and studies.
  */
 int prcg_trace_enable(prcg_ctx* ctx, int on);
 int prcg_trace_get(prcg_ctx* ctx, double* out, int slots);
