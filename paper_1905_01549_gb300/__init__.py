@@ -187,7 +187,8 @@ class BatchedSolver:
         torch = _torch()
         if x0 is None:
             x0 = torch.zeros(self.total, dtype=torch.float64, device="cuda")
-        key = autotune.batch_key(self.nx, self.ny, self.shift, self.precond, tol)
+        key = autotune.batch_key(self.nx, self.ny, self.shift, self.precond, tol,
+                                 torch.cuda.get_device_name())
         return autotune.tune(self.handle, b, x0, tol, maxit, key=key, **kw)
 
     def solve(self, b, x0=None, tol: float = 1e-8, maxit: int = 100000, true_relres: bool = False):

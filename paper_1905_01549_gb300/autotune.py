@@ -29,13 +29,32 @@ def default_cache_path() -> str:
     return os.path.join(os.path.expanduser("~"), ".cache", "prcg_gb300", "batched_tuning.json")
 
 
+_KERNEL_SOURCES = ("prcg_batched.cu", "prcg_reduce.cuh")
+
+
+def kernel_tag() -> str:
+    """Fingerprint of the batched kernel's sources: a cached choice is only
+    reused for the kernel it was measured on."""
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "csrc")
+    for f in _KERNEL_SOURCES:
+        try:
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+        except OSError:
+            h.update(f.encode())
+    return h.hexdigest()[:12]
+
+
 def batch_key(nx: Sequence[int], ny: Sequence[int], shift: Sequence[float], precond: int,
-              tol: float) -> str:
+              tol: float, device: str = "") -> str:
+    """Cache key: the batch's shape, preconditioner and tolerance, the kernel
+    version and the device the choice was measured on."""
     h = hashlib.sha256()
     for arr in (nx, ny):
         h.update(",".join(str(int(v)) for v in arr).encode())
     h.update(",".join(f"{float(v):.6g}" for v in shift).encode())
-    h.update(f"{precond}:{tol:.3g}".encode())
+    h.update(f"{precond}:{tol:.3g}:{device}:{kernel_tag()}".encode())
     return h.hexdigest()[:24]
 
 
