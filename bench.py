@@ -219,10 +219,10 @@ def make_solver(G, prob, op, precond):
                                  precond=precond)
 
 
-# Sources that define the SELL-32 sweeps and their launch configuration (the
-# kernels whose DRAM traffic profiles/traffic.json records).
-SWEEP_SOURCES = ("prcg_common.cuh", "prcg_reduce.cuh", "prcg_ops.cuh", "prcg_kernels.cuh",
-                 "prcg_tma.cuh", "prcg_launch.cuh", "prcg_inst_csr.cu")
+# Sources that define the TMA-staged SELL product sweep and its launch
+# configuration (the kernel whose DRAM traffic profiles/traffic.json records).
+SWEEP_SOURCES = ("prcg_common.cuh", "prcg_reduce.cuh", "prcg_ops.cuh", "prcg_tma.cuh",
+                 "prcg_launch.cuh", "prcg_inst_csr.cu")
 
 
 def kernel_source_hash() -> str:

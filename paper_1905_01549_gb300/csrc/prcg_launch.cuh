@@ -5,6 +5,7 @@
 
 #include "prcg_persistent.cuh"
 #include "prcg_tma.cuh"
+#include "prcg_mixed.cuh"
 
 namespace prcg {
 

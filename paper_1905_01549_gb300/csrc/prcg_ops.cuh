@@ -297,22 +297,6 @@ __device__ __forceinline__ double2 pc_pair(const Pc& pc, int i) {
   return make_double2(pc(i), pc(i + 1));
 }
 
-// The same for four rows (i a multiple of 4), rounded to FP32 for the
-// mixed-precision inner solve.
-template <class Pc>
-__device__ __forceinline__ float4 pc_quad32(const Pc& pc, int i) {
-  return make_float4((float)pc(i), (float)pc(i + 1), (float)pc(i + 2), (float)pc(i + 3));
-}
-
-// FP32 products of four consecutive rows i .. i+3 (i a multiple of 4) with
-// the FP32 vector p, in the order row32() adds them.  Generic form: four
-// gathered rows; the constant stencil overrides it (below).
-template <class Op>
-__device__ __forceinline__ float4 rows32x4(const Op& op, int i, const float* __restrict__ p) {
-  auto g = [&](int j) { return __ldg(p + j); };
-  return make_float4(op.row32(i, g), op.row32(i + 1, g), op.row32(i + 2, g), op.row32(i + 3, g));
-}
-
 template <class Op>
 struct IsDense : std::false_type {};
 template <>
@@ -339,57 +323,6 @@ struct PcVec {
 
 __device__ __forceinline__ double2 pc_pair(const PcVec& pc, int i) {
   return __ldg(reinterpret_cast<const double2*>(pc.d + i));
-}
-
-__device__ __forceinline__ float4 pc_quad32(const PcVec& pc, int i) {
-  const double2 a = __ldg(reinterpret_cast<const double2*>(pc.d + i));
-  const double2 b = __ldg(reinterpret_cast<const double2*>(pc.d + i + 2));
-  return make_float4((float)a.x, (float)a.y, (float)b.x, (float)b.y);
-}
-
-// Constant stencil, nx a multiple of 4: the four rows share y and z, so
-// their neighbours are four aligned 16-byte loads (y and z neighbours, the
-// rows themselves) and two scalars (the x neighbours outside the group).  A
-// missing neighbour gets coefficient 0 as in row32(), which then adds
-// 0 * p_i: the same FMA sequence, hence the same result.
-template <int DIM>
-__device__ __forceinline__ float4 rows32x4(const StencilOp<DIM>& op, int i,
-                                           const float* __restrict__ p) {
-  if (op.nx & 3) {
-    auto g = [&](int j) { return __ldg(p + j); };
-    return make_float4(op.row32(i, g), op.row32(i + 1, g), op.row32(i + 2, g), op.row32(i + 3, g));
-  }
-  const int nx = op.nx, ny = op.ny, nz = op.nz, pl = nx * ny;
-  const int x = i % nx, yz = i / nx, y = yz % ny, z = yz / ny;
-  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-  auto ld4 = [&](int j) { return __ldg(reinterpret_cast<const float4*>(p + j)); };
-  const float4 c = ld4(i);
-  const float lm = x > 0 ? __ldg(p + i - 1) : 0.f;
-  const float rp = x + 4 < nx ? __ldg(p + i + 4) : 0.f;
-  const float4 ym = y > 0 ? ld4(i - nx) : zero, yp = y < ny - 1 ? ld4(i + nx) : zero;
-  const float4 zm = DIM == 3 && z > 0 ? ld4(i - pl) : zero;
-  const float4 zp = DIM == 3 && z < nz - 1 ? ld4(i + pl) : zero;
-  const float cym = y > 0 ? -1.f : 0.f, cyp = y < ny - 1 ? -1.f : 0.f;
-  const float czm = z > 0 ? -1.f : 0.f, czp = z < nz - 1 ? -1.f : 0.f;
-  const float cd = (float)op.cdiag;
-  const float cv[4] = {c.x, c.y, c.z, c.w};
-  const float ymv[4] = {ym.x, ym.y, ym.z, ym.w}, ypv[4] = {yp.x, yp.y, yp.z, yp.w};
-  const float zmv[4] = {zm.x, zm.y, zm.z, zm.w}, zpv[4] = {zp.x, zp.y, zp.z, zp.w};
-  float out[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int xq = x + q;
-    float acc = 0.f;
-    if (DIM == 3) acc = fmaf(czm, zmv[q], acc);
-    acc = fmaf(cym, ymv[q], acc);
-    acc = fmaf(xq > 0 ? -1.f : 0.f, q == 0 ? lm : cv[q - 1 < 0 ? 0 : q - 1], acc);
-    acc = fmaf(cd, cv[q], acc);
-    acc = fmaf(xq < nx - 1 ? -1.f : 0.f, q == 3 ? rp : cv[q + 1 > 3 ? 3 : q + 1], acc);
-    acc = fmaf(cyp, ypv[q], acc);
-    if (DIM == 3) acc = fmaf(czp, zpv[q], acc);
-    out[q] = acc;
-  }
-  return make_float4(out[0], out[1], out[2], out[3]);
 }
 
 }  // namespace prcg
