@@ -143,7 +143,9 @@ class _Run:
 
     def log(self, k, x, r, rho):
         """Record ||r_k||/||b||; return True when the stopping test holds."""
-        rel = _sqrt(rho) / self.bnorm if self.bnorm > 0 else 0.0
+        # b == 0 counts as converged; a non-finite ||b|| stays non-finite, so
+        # the test fails and the variant breaks down on its scalars
+        rel = _sqrt(rho) / self.bnorm if self.bnorm != 0 else 0.0
         self.hist.append(rel)
         if self.record and k <= self.record:
             self.iterates.append((x.copy(), r.copy()))

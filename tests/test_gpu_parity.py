@@ -236,3 +236,58 @@ def test_persistent_and_graph_paths_match_oracle(G, torch_mod, name, op, precond
                 launches = binding.prcg_last_launches(S.handle)
                 assert (launches == 1) == (mode == "persistent"), (mode, launches)
         monkeypatch.delenv("PRCG_PERSIST_MAX", raising=False)
+
+
+@pytest.mark.parametrize("path", ["persistent", "graph"])
+def test_nan_in_b_reports_breakdown_and_context_recovers(G, torch_mod, path, monkeypatch):
+    """Host-side fault injection: a NaN in b makes the first scalars
+    non-finite; every variant stops with BREAKDOWN after initialize() (as the
+    oracle does), nothing hangs, and the context then solves normally."""
+    torch = torch_mod
+    if path == "graph":
+        monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    prob = case("poisson3d_ragged")
+    A = csr_matrix(prob)
+    bad = prob.b.copy()
+    bad[prob.n // 2] = np.nan
+    with make_solver(G, prob, "stencil", "jacobi") as S:
+        for variant in GPU_VARIANTS:
+            ref = O.solve(variant, A, bad, d=O.jacobi_inverse_diagonal(A), tol=1e-10, maxit=50)
+            res = S.solve(torch.from_numpy(bad).cuda(), variant=variant, tol=1e-10, maxit=50)
+            assert ref.status == O.BREAKDOWN
+            assert res.status == G.PRCG_BREAKDOWN and res.iters == ref.iters == 0, variant
+        res = S.solve(torch.from_numpy(prob.b).cuda(), variant="pr", tol=1e-10, maxit=1000)
+        assert res.status == G.PRCG_OK
+
+
+@pytest.mark.parametrize("path", ["persistent", "graph"])
+def test_exact_initial_guess_stops_at_zero_iterations(G, torch_mod, path, monkeypatch):
+    """x_0 = A^{-1} b exactly (integer x_0, integer stencil, so b = A x_0 and
+    r_0 = 0 in floating point): every variant returns OK with K = 0 and x_0."""
+    torch = torch_mod
+    if path == "graph":
+        monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    import problems as P
+    dims = (13, 9, 7)
+    x0 = np.random.default_rng(4).integers(-5, 6, 13 * 9 * 7).astype(np.float64)
+    b = P.stencil_apply(dims, x0)          # integers: exact, so r_0 = b - A x_0 = 0
+    with G.Solver.from_stencil(dims) as S:
+        for variant in GPU_VARIANTS:
+            x = torch.from_numpy(x0.copy()).cuda()
+            res = S.solve(torch.from_numpy(b).cuda(), x0=x, variant=variant, tol=1e-12, maxit=100,
+                          history=True)
+            assert res.status == G.PRCG_OK and res.iters == 0, variant
+            assert np.array_equal(x.cpu().numpy(), x0) and res.hist[0] == 0.0
+
+
+def test_graph_path_reruns_are_bitwise_identical(G, torch_mod, monkeypatch):
+    torch = torch_mod
+    monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    prob = case("varcoef3d_ragged")
+    b = torch.from_numpy(prob.b).cuda()
+    with make_solver(G, prob, "csr", "jacobi") as S:
+        for variant in GPU_VARIANTS:
+            r1 = S.solve(b, variant=variant, tol=1e-10, maxit=5000, history=True)
+            r2 = S.solve(b, variant=variant, tol=1e-10, maxit=5000, history=True)
+            assert r1.iters == r2.iters
+            assert torch.equal(r1.x, r2.x) and np.array_equal(r1.hist, r2.hist)

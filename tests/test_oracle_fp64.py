@@ -232,3 +232,19 @@ def test_jacobi_reduces_iterations_on_varcoef():
         assert none.status == O.OK and jac.status == O.OK
         assert jac.iters < none.iters
         assert O.true_relres(A, prob.b, jac.x) < 1e-9
+
+
+@pytest.mark.parametrize("variant", O.VARIANTS)
+def test_nonfinite_rhs_breaks_down_zero_rhs_converges(variant):
+    """Breakdown reading: any non-finite scalar stops the run with BREAKDOWN.
+    A NaN in b makes ||b|| and nu_0 NaN: the stopping test must not read the
+    NaN norm as b = 0, so the run breaks down after initialize().  b = 0 is
+    the converged case (x = 0, K = 0)."""
+    A = _poisson_sp((9, 7))
+    b = np.random.default_rng(3).uniform(-1, 1, 63)
+    bad = b.copy()
+    bad[10] = np.nan
+    res = O.solve(variant, A, bad, tol=1e-10, maxit=50)
+    assert res.status == O.BREAKDOWN and res.iters == 0
+    res = O.solve(variant, A, np.zeros(63), tol=1e-10, maxit=50)
+    assert res.status == O.OK and res.iters == 0 and not res.x.any()
