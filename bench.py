@@ -355,6 +355,7 @@ def run_ours(args):
         line["autograd"] = run_autograd(G, args)
         line["convergence"] = run_convergence(G, args)
         line["dense_model"] = run_dense(G, args)
+        line["sync_bound"] = run_sync_bound(G, args)
         if world == 1:
             line["cpu_baseline"] = run_cpu_baseline(prob, variant, precond, args)
     S.close()
@@ -585,6 +586,42 @@ def run_convergence(G, args):
                        "min_log10_err": round(r["min_log10_err"], 2),
                        "paper": PAPER_TABLE2_MODEL_48_8_3[pc][v]} for v, r in st.items()}
     out["seconds"] = round(time.perf_counter() - t0, 2)
+    return out
+
+
+def run_sync_bound(G, args):
+    """The synchronisation-bound regime: 2D 5-point Poisson 64 x 64 (n = 4096),
+    CSR, no preconditioner, x_true ~ U(-1, 1), b = A x_true, every variant to
+    1e-10 (maxit 2n), as one persistent kernel and as the graph of sweeps.
+    Device time of the whole solve (best of 5) and per iteration: the order
+    follows the synchronisations per iteration (Table 1)."""
+    import torch
+    import problems as P
+    prob = P.poisson2d_64()
+    rp, ci, v = prob.csr
+    b = torch.from_numpy(prob.b).cuda()
+    out = {"workload": "poisson2d_64 CSR, no preconditioner, tol 1e-10, maxit 2n"}
+    saved = os.environ.get("PRCG_PERSIST_MAX")
+    try:
+        for path, bound in (("persistent", str(1 << 21)), ("graph", "0")):
+            os.environ["PRCG_PERSIST_MAX"] = bound
+            row = {}
+            with G.Solver.from_csr(rp, ci, v) as S:
+                for var in ("hs", "cgcg", "m", "pr", "gv", "pipe_m", "pipe_pr"):
+                    best = None
+                    for _ in range(5):
+                        r = S.solve(b, variant=var, tol=1e-10, maxit=2 * prob.n)
+                        t = r.init_ms + r.loop_ms
+                        if best is None or t < best[0]:
+                            best = (t, r.iters, r.status)
+                    row[var] = {"ms": round(best[0], 4), "iters": best[1], "status": best[2],
+                                "us_per_iter": round(1e3 * best[0] / max(best[1], 1), 2)}
+            out[path] = row
+    finally:
+        if saved is None:
+            os.environ.pop("PRCG_PERSIST_MAX", None)
+        else:
+            os.environ["PRCG_PERSIST_MAX"] = saved
     return out
 
 
