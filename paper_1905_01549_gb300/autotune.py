@@ -19,7 +19,7 @@ from . import binding
 
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = (
     (1, 256), (1, 512), (1, 1024), (2, 256), (2, 512), (4, 256), (4, 512), (8, 256), (8, 512),
-    (16, 256))
+    (8, 1024), (16, 256), (16, 512), (16, 1024))
 
 
 def default_cache_path() -> str:
