@@ -18,6 +18,15 @@
  *   PRCG_M, PRCG_PIPE_M, PRCG_CGCG, PRCG_GV are the Appendix E variants
  *                 (M-CG, pipe-PR-M-CG, Chronopoulos-Gear CG in 2 sweeps,
  *                 Ghysels-Vanroose pipelined CG in 1 sweep per iteration).
+ *   PRCG_PR_NO_RECOMPUTE, PRCG_PIPE_PR_NO_RECOMPUTE are the ablations the
+ *                 paper's analysis compares against: PR-CG whose scalar
+ *                 recurrences continue from the predicted nu'_k instead of
+ *                 the recomputed nu_k (Section 3.1, Fig. 1; nu' may turn
+ *                 negative once ||r_k|| ~ sqrt(eps), which reports
+ *                 PRCG_BREAKDOWN), and pipe-PR-CG that carries w_k = w'_k
+ *                 instead of recomputing A r~_k (Section 3.2, Fig. 2: the
+ *                 w'-gap accumulates).  Same sweeps as PRCG_PR and
+ *                 PRCG_PIPE_PR (the pipe ablation forms only u = A s~).
  *
  * Threading: a context is not thread-safe; use one context per host thread.
  * All work of a context runs on the CUDA stream given at creation (or the
@@ -49,7 +58,9 @@ enum prcg_variant {
     PRCG_M = 3,
     PRCG_PIPE_M = 4,
     PRCG_CGCG = 5,
-    PRCG_GV = 6
+    PRCG_GV = 6,
+    PRCG_PR_NO_RECOMPUTE = 7,
+    PRCG_PIPE_PR_NO_RECOMPUTE = 8
 };
 
 enum prcg_precond {
@@ -145,10 +156,10 @@ int prcg_create_dense(prcg_ctx** out, int64_t n, const double* A, int precond, v
  * three) or a negative error (x untouched).  If b == 0, x is set to 0 and
  * K = 0.  The call blocks until the result is on the host.
  * Execution: for n <= 2^21 (dense contexts: n <= 4096; the environment
- * variable PRCG_PERSIST_MAX lowers the bound) every variant runs as one
- * persistent cooperative kernel (grid barriers instead of kernel
- * boundaries); larger systems run as one CUDA graph launch with a
- * device-side while loop.
+ * variable PRCG_PERSIST_MAX lowers the bound) every variant but the two
+ * ablations runs as one persistent cooperative kernel (grid barriers
+ * instead of kernel boundaries); larger systems, and the ablations at every
+ * size, run as one CUDA graph launch with a device-side while loop.
  */
 int prcg_solve(prcg_ctx* ctx, int variant, const double* b, double* x,
                double tol, int maxit, double* residual_history,
@@ -230,6 +241,7 @@ int prcg_last_timing(const prcg_ctx* ctx, float* init_ms, float* loop_ms, int* i
  *                 dense context a product sweep's time includes its product
  *                 kernel.  The sweeps are those of the graph path.
  *   nsweeps       receives the number of sweeps written (3, 2 or 1)
+ * The two ablation variants are not timed (PRCG_ERR_UNSUPPORTED).
  */
 int prcg_time_sweeps(prcg_ctx* ctx, int variant, int reps, float* ms_per_sweep, int* nsweeps);
 

@@ -16,14 +16,18 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libprcg.so")
 
-PRCG_HS, PRCG_PR, PRCG_PIPE_PR, PRCG_M, PRCG_PIPE_M, PRCG_CGCG, PRCG_GV = range(7)
+(PRCG_HS, PRCG_PR, PRCG_PIPE_PR, PRCG_M, PRCG_PIPE_M, PRCG_CGCG, PRCG_GV,
+ PRCG_PR_NO_RECOMPUTE, PRCG_PIPE_PR_NO_RECOMPUTE) = range(9)
 PRCG_PRECOND_NONE, PRCG_PRECOND_JACOBI = 0, 1
 PRCG_OK, PRCG_NOT_CONVERGED, PRCG_BREAKDOWN = 0, 1, 2
 PRCG_ERR_INVALID, PRCG_ERR_CUDA, PRCG_ERR_OOM, PRCG_ERR_TIMEOUT, PRCG_ERR_UNSUPPORTED = \
     -1, -2, -3, -4, -5
 
 VARIANT_IDS = {"hs": PRCG_HS, "pr": PRCG_PR, "pipe_pr": PRCG_PIPE_PR, "m": PRCG_M,
-               "pipe_m": PRCG_PIPE_M, "cgcg": PRCG_CGCG, "gv": PRCG_GV}
+               "pipe_m": PRCG_PIPE_M, "cgcg": PRCG_CGCG, "gv": PRCG_GV,
+               # the no-recompute ablations of Section 3 (Figs. 1 and 2)
+               "pr_norecompute": PRCG_PR_NO_RECOMPUTE,
+               "pipe_pr_norecompute": PRCG_PIPE_PR_NO_RECOMPUTE}
 STATUS_NAMES = {0: "OK", 1: "NOT_CONVERGED", 2: "BREAKDOWN", -1: "ERR_INVALID", -2: "ERR_CUDA",
                 -3: "ERR_OOM", -4: "ERR_TIMEOUT", -5: "ERR_UNSUPPORTED"}
 

@@ -270,7 +270,7 @@ struct prcg_ctx {
   double* hist = nullptr;
   int hist_cap = 0;
   int* dbad = nullptr;
-  VariantGraph graphs[8];
+  VariantGraph graphs[10];
   bool use_graph = true;
   float t_init = 0.f, t_loop = 0.f;
   int last_iters = 0;
@@ -437,6 +437,7 @@ int iter_launches(int variant) {
     case V_HS: return 3;
     case V_PR:
     case V_M:
+    case V_PR_NR:
     case V_CGCG: return 2;
     default: return 1;
   }
@@ -453,6 +454,7 @@ int launch_iter(prcg_ctx* c, int variant, int qr, int qw, cudaStream_t st) {
       break;
     case V_PR:
     case V_M:
+    case V_PR_NR:
       CK(c->launch(c->plan, PH_PR_A, variant, qr, qw, st));
       CK(c->launch(c->plan, PH_PR_B, variant, qr, qw, st));
       break;
@@ -467,6 +469,9 @@ int launch_iter(prcg_ctx* c, int variant, int qr, int qw, cudaStream_t st) {
     case V_GV:
       CK(c->launch(c->plan, PH_GV, variant, qr, qw, st));
       break;
+    case V_PIPE_NR:
+      CK(c->launch(c->plan, PH_PIPE_NR, variant, qr, qw, st));
+      break;
     default:
       return set_err(c, PRCG_ERR_UNSUPPORTED, "variant not built on the GPU path");
   }
@@ -475,7 +480,7 @@ int launch_iter(prcg_ctx* c, int variant, int qr, int qw, cudaStream_t st) {
 
 int chunk_for(prcg_ctx* c) { return c->n >= (1 << 20) ? 2 : 16; }
 
-constexpr int kMixedGraph = 7;   // graphs[7]: the FP32 inner solve of the mixed form
+constexpr int kMixedGraph = 9;   // graphs[9]: the FP32 inner solve of the mixed form
 
 int launch_mixed_init(prcg_ctx* c, cudaStream_t st) {
   CK(c->launch(c->plan, PH_MX_INIT_A, 0, 0, 0, st));
@@ -835,7 +840,7 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   if (!c) return set_err(nullptr, PRCG_ERR_INVALID, "ctx is NULL");
   if (!b || !x) return set_err(c, PRCG_ERR_INVALID, "b or x is NULL");
   if (!(tol >= 0.0) || maxit < 0) return set_err(c, PRCG_ERR_INVALID, "tol < 0 or maxit < 0");
-  if (variant < 0 || variant > 6) return set_err(c, PRCG_ERR_INVALID, "unknown variant");
+  if (variant < 0 || variant > V_PIPE_NR) return set_err(c, PRCG_ERR_INVALID, "unknown variant");
   const int n = c->n;
   int rc;
   if (c->hist_cap < maxit + 1) {
@@ -852,7 +857,9 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   // product (one 1024-thread CTA per SM) by ~11 % at n = 10752.
   const int persist_max =
       c->plan.op.kind == OP_DENSE ? std::min(c->persist_max, kDensePersistMax) : c->persist_max;
-  const bool persist = n <= persist_max;   // every variant has a persistent form
+  // every variant but the two no-recompute ablations has a persistent form
+  const bool ablation = variant == V_PR_NR || variant == V_PIPE_NR;
+  const bool persist = n <= persist_max && !ablation;
   bool graph = !persist && c->use_graph;
   if (graph && build_graph(c, variant) != PRCG_OK) graph = false;  // fall back to the host loop
   const int chunk = graph ? c->graphs[variant].chunk : chunk_for(c);
@@ -880,6 +887,7 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   h.maxit = maxit;
   h.maxbodies = maxit / chunk + 3;
   h.status = kRunning;
+  h.carry_nu = variant == V_PR_NR ? 1 : 0;
   CK(cudaMemcpyAsync(c->S, &h, sizeof h, cudaMemcpyHostToDevice, c->cs));
   CK(cudaEventRecord(c->ev_start, c->cs));
   bool persisted = false;
@@ -974,7 +982,8 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
 
 int prcg_time_sweeps(prcg_ctx* c, int variant, int reps, float* ms_per_sweep, int* nsweeps) {
   if (!c || !ms_per_sweep || !nsweeps || reps < 1) return set_err(c, PRCG_ERR_INVALID, "bad argument");
-  if (variant < 0 || variant > 6) return set_err(c, PRCG_ERR_UNSUPPORTED, "variant not built");
+  if (variant < 0 || variant > 6)
+    return set_err(c, PRCG_ERR_UNSUPPORTED, "variant not timed (unknown or an ablation)");
   int phases[3];
   int np = 0;
   if (variant == V_HS) {

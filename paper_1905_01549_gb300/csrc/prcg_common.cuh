@@ -18,7 +18,12 @@ constexpr int kMaxGrid = 152 * 16;      // upper bound of CTAs of one sweep
 constexpr int kMaxNV = 8;               // doubles reduced per CTA
 constexpr int kRunning = -100;          // status while the loop runs
 
-enum Variant { V_HS = 0, V_PR = 1, V_PIPE = 2, V_M = 3, V_PIPE_M = 4, V_CGCG = 5, V_GV = 6 };
+enum Variant {
+  V_HS = 0, V_PR = 1, V_PIPE = 2, V_M = 3, V_PIPE_M = 4, V_CGCG = 5, V_GV = 6,
+  // the no-recompute ablations: PR-CG with nu_k carried as nu'_k (Section 3.1,
+  // Fig. 1) and pipe-PR-CG with w_k carried as w'_k (Section 3.2, Fig. 2)
+  V_PR_NR = 7, V_PIPE_NR = 8
+};
 
 // Device-resident scalar block (one per context).  Written by the last CTA
 // of each sweep after the grid reduction, read by every CTA of the next.
@@ -44,6 +49,7 @@ struct DevState {
   int profile;           // timing runs: never finish, keep every sweep doing its work
   double arg;            // mixed precision: 1 / ||t|| of the current refinement step
   double* trace;         // optional scalar trace, (maxit + 2) x kTraceFields, or NULL
+  int carry_nu;          // 1: nu_k := nu'_k for k >= 1 (the PR-CG ablation of Fig. 1)
 };
 
 // Scalar trace: slot k holds the scalars of iteration k in the oracle's
@@ -171,8 +177,13 @@ __device__ __forceinline__ void breakdown(DevState* S) {
 
 // alpha_k = nu_k / mu_k and, for the predict-and-recompute variants,
 // nu'_{k+1} (Eq. 2.3, or Meurant's form) and beta_{k+1} = nu'_{k+1} / nu_k.
+//
+// With carry_nu the recomputed <r~_k, r_k> in S->nu is only recorded: the
+// scalar recurrences continue from the predicted nu'_k of the previous step,
+// still in S->nu_pred (nu_0 is always the inner product of initialize()).
 __device__ __forceinline__ void scalar_step_pr(DevState* S, bool meurant) {
-  const double nu = S->nu, mu = S->mu, sigma = S->sigma, gamma = S->gamma;
+  const double nu = (S->carry_nu && S->k > 0) ? S->nu_pred : S->nu;
+  const double mu = S->mu, sigma = S->sigma, gamma = S->gamma;
   if (!finite(nu) || !finite(mu) || !(mu > 0.0) || nu < 0.0) { breakdown(S); return; }
   const double alpha = nu / mu;
   double nu_pred;

@@ -74,8 +74,9 @@ template <class Op, class Pc>
 __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevState* S,
                                                    double* partials, int variant) {
   if (__ldcg(&S->done)) return;
-  const bool pipe = variant == V_PIPE || variant == V_PIPE_M || variant == V_GV;
-  const bool keep_w = variant == V_CGCG || variant == V_GV;
+  const bool pipe = variant == V_PIPE || variant == V_PIPE_M || variant == V_GV ||
+                    variant == V_PIPE_NR;
+  const bool keep_w = variant == V_CGCG || variant == V_GV || variant == V_PIPE_NR;
   double acc[3] = {0.0, 0.0, 0.0};
   const double* __restrict__ p = V.p[0];
   PRCG_ROWS(i, op.n) {
@@ -85,6 +86,7 @@ __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevStat
     if (Pc::on && pipe) V.st[0][i] = st;
     if (keep_w) V.w[0][i] = s;   // w_0 = A r~_0 is the same product (p_0 = r~_0)
     if (variant == V_GV) V.u[0][i] = 0.0;   // multiplied by beta_0 = 0 in the first sweep
+    if (variant == V_PIPE_NR && Pc::on) V.u[0][i] = st;   // w~_0 = M^{-1} w_0
     const double pi = __ldg(p + i);
     const double rt = Pc::on ? __ldg(V.rt[0] + i) : __ldg(V.r[0] + i);
     acc[0] += pi * s;
@@ -99,7 +101,8 @@ __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevStat
     trace(S, 0, TR_MU, tot[0]);
     trace(S, 0, TR_SIGMA, tot[1]);
     trace(S, 0, TR_GAMMA, tot[2]);
-    if (variant == V_PR || variant == V_PIPE || variant == V_M || variant == V_PIPE_M) {
+    if (variant == V_PR || variant == V_PIPE || variant == V_M || variant == V_PIPE_M ||
+        variant == V_PR_NR || variant == V_PIPE_NR) {
       scalar_step_pr(S, variant == V_M || variant == V_PIPE_M);
     } else {
       const double nu = S->nu, mu = tot[0];
@@ -407,6 +410,72 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
     S->rho = tot[4];
     trace_pr_sums(S, k);
     if (!record_and_test(S, k, tot[4])) scalar_step_pr(S, meurant != 0);
+  }
+}
+
+// ------------------------------------- pipe-PR-CG without recomputing w
+// The ablation of Section 3.2 (Eq. 3.23, Fig. 2): w_k is never recomputed as
+// A r~_k but carried as w'_k = w_{k-1} - alpha_{k-1} u_{k-1}, and under Jacobi
+// w~_k as w~'_k = w~_{k-1} - alpha_{k-1} M^{-1} u_{k-1}, so each sweep forms
+// the single product u_{k-1} = A s~_{k-1}.  The carried w and w~ live in
+// V.w[0] and V.u[0] (each row reads and rewrites only its own entry); every
+// other step is k_pipe's.
+template <class Op, class Pc>
+__global__ void __launch_bounds__(kBlock) k_pipe_nr(Op op, Pc pc, Vecs V, DevState* S,
+                                                    double* partials, int qr, int qw) {
+  if (__ldcg(&S->done)) return;
+  const double alpha = __ldcg(&S->alpha);
+  const double beta = __ldcg(&S->beta);
+  const double* __restrict__ rt_o = Pc::on ? V.rt[qr] : V.r[qr];
+  const double* __restrict__ st_o = Pc::on ? V.st[qr] : V.s[qr];
+  const double* __restrict__ r_o = V.r[qr];
+  const double* __restrict__ s_o = V.s[qr];
+  double* __restrict__ x = V.x;
+  double* __restrict__ p = V.p[0];
+  double* __restrict__ w = V.w[0];
+  double* __restrict__ wt = V.u[0];
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+  PRCG_ROWS(i, op.n) {
+    const double u = op.row(i, [&](int j) { return __ldg(st_o + j); });
+    const double si = __ldg(s_o + i);
+    x[i] = fma(alpha, p[i], x[i]);
+    const double rn = fma(-alpha, si, __ldg(r_o + i));
+    const double wp = fma(-alpha, u, w[i]);
+    w[i] = wp;
+    double rtn = rn, sn, stn;
+    if (Pc::on) {
+      const double sti = __ldg(st_o + i);
+      rtn = fma(-alpha, sti, __ldg(rt_o + i));
+      const double wtp = fma(-alpha, pc(i) * u, wt[i]);
+      wt[i] = wtp;
+      sn = fma(beta, si, wp);
+      stn = fma(beta, sti, wtp);
+      V.rt[qw][i] = rtn;
+      V.st[qw][i] = stn;
+    } else {
+      sn = fma(beta, si, wp);
+      stn = sn;
+    }
+    const double pn = fma(beta, p[i], rtn);
+    p[i] = pn;
+    V.r[qw][i] = rn;
+    V.s[qw][i] = sn;
+    acc[0] = fma(pn, sn, acc[0]);
+    acc[1] = fma(rtn, sn, acc[1]);
+    acc[2] = fma(stn, sn, acc[2]);
+    if (Pc::on) acc[3] = fma(rtn, rn, acc[3]);
+    acc[4] = fma(rn, rn, acc[4]);
+  }
+  double tot[5];
+  if (grid_sum<5>(acc, partials, S, tot) && threadIdx.x == 0) {
+    const int k = S->k + 1;
+    S->mu = tot[0];
+    S->sigma = tot[1];
+    S->gamma = tot[2];
+    S->nu = Pc::on ? tot[3] : tot[4];
+    S->rho = tot[4];
+    trace_pr_sums(S, k);
+    if (!record_and_test(S, k, tot[4])) scalar_step_pr(S, false);
   }
 }
 

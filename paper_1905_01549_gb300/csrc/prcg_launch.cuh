@@ -28,8 +28,9 @@ enum Phase {
   PH_CG_A = 15,
   PH_CG_B = 16,
   PH_GV = 17,
-  PH_PERSIST = 18,  // the whole solve as one cooperative launch (HS, PR, M, pipe, pipe-M)
-  PH_ANORM = 19     // ||x* - x||_A^2 (x* in V.t, x in V.w[1]) into S->eta
+  PH_PERSIST = 18,  // the whole solve as one cooperative launch (all but the ablations)
+  PH_ANORM = 19,    // ||x* - x||_A^2 (x* in V.t, x in V.w[1]) into S->eta
+  PH_PIPE_NR = 20   // pipe-PR-CG with w carried instead of recomputed (ablation)
 };
 
 struct Plan {
@@ -156,6 +157,7 @@ cudaError_t dense_prepass(const Plan& P, const Op& op, int phase, int qr, cudaSt
         nv = 2;
         break;
       case PH_CG_B: s0.a = Pc::on ? V.rt[0] : V.r[0]; break;
+      case PH_PIPE_NR: s0.a = Pc::on ? V.st[qr] : V.s[qr]; break;
       case PH_GV:
         s0.a = V.w[qr];
         if (Pc::on) s0.scale = P.pc.d;
@@ -257,6 +259,11 @@ cudaError_t launch_phase(const Plan& P, int phase, int variant, int qr, int qw, 
       }
       auto k = k_pipe<Op, Pc>;
       k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw, meurant);
+      break;
+    }
+    case PH_PIPE_NR: {
+      auto k = k_pipe_nr<Op, Pc>;
+      k<<<grid_for(k, n, P.sms), kBlock, 0, st>>>(op, pc, P.v, P.S, P.partials, qr, qw);
       break;
     }
     case PH_CG_A: {

@@ -52,7 +52,7 @@ def _fsum_dot(a, b):
     return math.fsum(a * b)
 
 
-def oracle_spread(variant, A, b, d, k):
+def oracle_spread(variant, A, b, d, k, **kw):
     """Rounding sensitivity of the iterates themselves: the oracle against the
     same oracle with exactly rounded inner products (math.fsum).  On
     ill-conditioned systems (unpreconditioned log-normal diffusion, sigma = 2)
@@ -60,11 +60,11 @@ def oracle_spread(variant, A, b, d, k):
     implementation can match another to 1e-10 there; the bar becomes
     max(1e-10, 100 x this spread)."""
     import oracle.cg_variants as CV
-    ref = O.solve(variant, A, b, d=d, tol=0.0, maxit=k)
+    ref = O.solve(variant, A, b, d=d, tol=0.0, maxit=k, **kw)
     saved = CV._dot
     CV._dot = lambda u, v: saved(u, v) if u.dtype == object else _fsum_dot(u, v)
     try:
-        alt = O.solve(variant, A, b, d=d, tol=0.0, maxit=k)
+        alt = O.solve(variant, A, b, d=d, tol=0.0, maxit=k, **kw)
     finally:
         CV._dot = saved
     hs = np.asarray(ref.hist)

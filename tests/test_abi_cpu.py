@@ -65,3 +65,21 @@ def test_no_cpu_fallback_in_product_path():
     for f in glob.glob(os.path.join(pkg, "**", "*.py"), recursive=True):
         src = open(f).read()
         assert "import oracle" not in src and "from oracle" not in src, f
+
+
+def _header_enum(name):
+    src = open(os.path.join(ROOT, "include", "prcg.h")).read()
+    body = re.search(r"enum\s+" + name + r"\s*\{(.*?)\}", src, flags=re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return {k: int(v) for k, v in re.findall(r"\b(PRCG_[A-Z_]+)\s*=\s*(-?\d+)", body)}
+
+
+def test_binding_variant_ids_match_header():
+    """Every variant the header declares is reachable from Python by name,
+    with the header's value."""
+    from paper_1905_01549_gb300 import binding
+    enum = _header_enum("prcg_variant")
+    assert len(enum) == 9
+    for k, v in enum.items():
+        assert getattr(binding, k) == v, k
+    assert sorted(binding.VARIANT_IDS.values()) == sorted(enum.values())
