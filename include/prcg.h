@@ -293,6 +293,23 @@ int prcg_inject_barrier_skip(prcg_ctx* ctx, int cta, int barrier, int64_t spin_l
 int prcg_check_guards(prcg_ctx* ctx, int64_t* corrupted_out);
 
 /*
+ * prcg_test_neighbour_sum -- run the constant-coefficient stencil's
+ * neighbour sum on the device for count tuples of `terms` doubles (4: the
+ * 2D 5-point stencil, 6: the 3D 7-point stencil), for tests of that kernel
+ * arithmetic.  The sum is formed in 64-bit fixed point aligned to the
+ * largest term and rounded once to nearest-even (error at most one rounding
+ * of the exact sum plus terms * 2^-59 times the largest term); tuples with a
+ * non-finite term, a term of magnitude >= 2^1018, or all terms below 2^-959
+ * are added in sequential FP64 instead, so NaN and infinity propagate.
+ *   v     host or device, count x terms doubles, tuple-major
+ *   out   host or device, count doubles
+ * Returns PRCG_OK, PRCG_ERR_INVALID (terms not 4 or 6, count < 0, NULL
+ * arrays) or a CUDA error; prcg_last_error(NULL) describes a failure.
+ * Blocks until out is written; allocates and frees its own device buffers.
+ */
+int prcg_test_neighbour_sum(int terms, const double* v, int64_t count, double* out);
+
+/*
  * prcg_trace_enable -- record, during every later prcg_solve on ctx (on != 0)
  * or no more (on == 0), the scalars each iteration forms.  Costs a few
  * device stores per iteration and a buffer of (maxit + 2) x 10 doubles.

@@ -37,7 +37,7 @@ EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_create_dense", "prcg_
            "prcg_grad_faces", "prcg_grad_csr_values",
            "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n", "prcg_error_anorm",
            "prcg_trace_enable", "prcg_trace_get", "prcg_check_guards",
-           "prcg_inject_barrier_skip",
+           "prcg_inject_barrier_skip", "prcg_test_neighbour_sum",
            "prcg_pr_solve_stencil_noalloc", "prcg_batched_create", "prcg_batched_configure",
            "prcg_batched_solve", "prcg_batched_last_ms", "prcg_batched_config",
            "prcg_batched_last_error", "prcg_batched_destroy")
@@ -104,6 +104,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.prcg_inject_barrier_skip.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int64]
     lib.prcg_inject_barrier_skip.restype = ctypes.c_int
     lib.prcg_check_guards.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.prcg_test_neighbour_sum.argtypes = [ctypes.c_int, vp, ctypes.c_int64, vp]
+    lib.prcg_test_neighbour_sum.restype = ctypes.c_int
     lib.prcg_check_guards.restype = ctypes.c_int
     lib.prcg_trace_enable.argtypes = [vp, ctypes.c_int]
     lib.prcg_trace_enable.restype = ctypes.c_int
@@ -274,6 +276,19 @@ def prcg_check_guards(ctx) -> int:
     bad = ctypes.c_int64(0)
     _check(load().prcg_check_guards(ctx, ctypes.byref(bad)), ctx)
     return int(bad.value)
+
+
+def prcg_test_neighbour_sum(v) -> "np.ndarray":
+    """The stencil's device neighbour sum of each row of v (float64, shape
+    (count, 4) or (count, 6)); a test hook for that kernel arithmetic."""
+    import numpy as np
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    if v.ndim != 2:
+        raise ValueError("v must be (count, terms)")
+    out = np.empty(v.shape[0], dtype=np.float64)
+    _check(load().prcg_test_neighbour_sum(int(v.shape[1]), v.ctypes.data, int(v.shape[0]),
+                                          out.ctypes.data), None)
+    return out
 
 
 TRACE_FIELDS = ("alpha", "beta", "nu", "nu_pred", "mu", "sigma", "gamma", "rho", "eta", "unused")

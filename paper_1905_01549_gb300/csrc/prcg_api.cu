@@ -647,6 +647,38 @@ int copy_in(prcg_ctx* c, void* dst, const void* src, size_t bytes) {
   return PRCG_OK;
 }
 
+// Test kernel: the stencil operators' neighbour sum over count K-tuples.
+template <int K>
+__global__ void k_test_neighbour_sum(const double* __restrict__ v, int64_t count,
+                                     double* __restrict__ out) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < count;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    double a[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) a[j] = v[t * K + j];
+    out[t] = neighbour_sum<K>(a);
+  }
+}
+
+// Host spot check of the invariant-divisor quotient the stencil sweeps use
+// for every dividend 0 <= v < limit: the end points, and the neighbourhood of
+// the multiples of d near the top of the range, where a wrong multiplier
+// fails first.
+bool fastdiv_ok(const FastDiv& f, int d, int limit) {
+  auto ok = [&](long long v) {
+    return v < 0 || v >= limit || fast_div(f, (int)v) == (int)(v / d);
+  };
+  if (!ok(0) || !ok(limit - 1)) return false;
+  const long long top = (long long)(limit - 1) / d;
+  for (long long q = top; q >= 0 && q > top - 64; --q)
+    for (long long e = -2; e <= 2; ++e)
+      if (!ok(q * d + e)) return false;
+  for (long long q = 0; q < 64; ++q)
+    for (long long e = -2; e <= 2; ++e)
+      if (!ok(q * d + e)) return false;
+  return true;
+}
+
 }  // namespace
 
 extern "C" {
@@ -745,6 +777,10 @@ int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t
   op.nx = (int)nx;
   op.ny = (int)ny;
   op.nz = (int)nz;
+  op.divx = make_fastdiv(op.nx);
+  op.divy = make_fastdiv(op.ny);
+  if (!fastdiv_ok(op.divx, op.nx, op.n) || !fastdiv_ok(op.divy, op.ny, op.n / op.nx))
+    return fail(set_err(c, PRCG_ERR_INVALID, "internal: stencil coordinate division check failed"));
   c->precond = precond;
   if (!face_coeff) {
     op.kind = dim == 2 ? OP_ST2 : OP_ST3;
@@ -1315,6 +1351,31 @@ int prcg_check_guards(prcg_ctx* c, int64_t* corrupted_out) {
   CK(cudaStreamSynchronize(c->cs));
   *corrupted_out = (int64_t)bad;
   return PRCG_OK;
+}
+
+int prcg_test_neighbour_sum(int terms, const double* v, int64_t count, double* out) {
+  prcg_ctx* c = nullptr;   // no context: errors go to prcg_last_error(NULL)
+  if ((terms != 4 && terms != 6) || count < 0 || (count > 0 && (!v || !out)))
+    return set_err(c, PRCG_ERR_INVALID, "terms must be 4 or 6, count >= 0, v and out non-NULL");
+  if (count == 0) return PRCG_OK;
+  double* dv = nullptr;
+  double* dout = nullptr;
+  const size_t bin = (size_t)count * terms * sizeof(double), bout = (size_t)count * sizeof(double);
+  cudaError_t e = cudaMalloc(&dv, bin);
+  if (e == cudaSuccess) e = cudaMalloc(&dout, bout);
+  if (e == cudaSuccess) e = cudaMemcpy(dv, v, bin, cudaMemcpyDefault);
+  if (e == cudaSuccess) {
+    const int64_t blocks = std::min<int64_t>((count + 255) / 256, 4096);
+    if (terms == 4)
+      k_test_neighbour_sum<4><<<(int)blocks, 256>>>(dv, count, dout);
+    else
+      k_test_neighbour_sum<6><<<(int)blocks, 256>>>(dv, count, dout);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, bout, cudaMemcpyDefault);
+  if (dv) cudaFree(dv);
+  if (dout) cudaFree(dout);
+  return e == cudaSuccess ? PRCG_OK : cuda_err(c, e, "neighbour sum test");
 }
 
 int prcg_trace_enable(prcg_ctx* c, int on) {

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "../../include/prcg.h"
+#include "prcg_isum.cuh"
 #include "prcg_reduce.cuh"
 
 namespace cg = cooperative_groups;
@@ -34,6 +35,7 @@ struct BatchSys {
   int nx, ny;
   double cdiag;   // 4 + shift
   double d;       // Jacobi 1 / cdiag, or 1
+  prcg::FastDiv divx;   // division by nx
 };
 
 constexpr int kMaxThreads = 1024;
@@ -75,15 +77,18 @@ __device__ __forceinline__ void cluster_sum(double (&v)[NV], double* sm, double*
   parity ^= 1;
 }
 
+// (A v)_i = cdiag v_i - sum of the existing neighbours; the neighbour sum is
+// exact in fixed point on the integer pipes and rounded once
+// (prcg_isum.cuh), leaving one FP64 FMA per row.
 __device__ __forceinline__ double stencil_row(const BatchSys& q, const double* __restrict__ v, int i) {
-  const int x = i % q.nx, y = i / q.nx;
-  double acc = 0.0;
-  if (y > 0) acc = fma(-1.0, __ldcg(v + i - q.nx), acc);
-  if (x > 0) acc = fma(-1.0, __ldcg(v + i - 1), acc);
-  acc = fma(q.cdiag, __ldcg(v + i), acc);
-  if (x < q.nx - 1) acc = fma(-1.0, __ldcg(v + i + 1), acc);
-  if (y < q.ny - 1) acc = fma(-1.0, __ldcg(v + i + q.nx), acc);
-  return acc;
+  const int y = prcg::fast_div(q.divx, i), x = i - y * q.nx;
+  const double ym = __ldcg(v + (y > 0 ? i - q.nx : i));
+  const double xm = __ldcg(v + (x > 0 ? i - 1 : i));
+  const double xp = __ldcg(v + (x < q.nx - 1 ? i + 1 : i));
+  const double yp = __ldcg(v + (y < q.ny - 1 ? i + q.nx : i));
+  const double nb[4] = {y > 0 ? ym : 0.0, x > 0 ? xm : 0.0, x < q.nx - 1 ? xp : 0.0,
+                        y < q.ny - 1 ? yp : 0.0};
+  return fma(q.cdiag, __ldcg(v + i), -prcg::neighbour_sum<4>(nb));
 }
 
 struct BatchArgs {
@@ -401,6 +406,7 @@ int prcg_batched_create(prcg_batch** out, int nsys, const int32_t* nx, const int
     sys[i].ny = ny[i];
     sys[i].cdiag = 4.0 + shift[i];
     sys[i].d = precond == PRCG_PRECOND_JACOBI ? 1.0 / sys[i].cdiag : 1.0;
+    sys[i].divx = prcg::make_fastdiv(nx[i]);
     const double n = (double)nx[i] * ny[i];
     // work ~ n * sqrt(condition number): lambda_min of the shifted 5-point
     // operator is 2 - 2 cos(pi/(nx+1)) + 2 - 2 cos(pi/(ny+1)) + shift

@@ -22,6 +22,21 @@
 
 namespace prcg {
 
+// CTAs per SM the single-product sweeps ask the register allocator for.
+// The constant stencil's product sweeps are bound by integer issue and
+// memory latency (their neighbour sums run on the integer pipes), so they
+// want every warp slot: 8 CTAs of 256 threads, 32 registers a thread.  0
+// leaves the allocator its own choice (the other operators, and the
+// two-product pipelined sweep, which would spill at 32 registers).
+template <class Op>
+struct SweepMinBlocks {
+  static constexpr int value = 0;
+};
+template <int DIM>
+struct SweepMinBlocks<StencilOp<DIM>> {
+  static constexpr int value = 8;
+};
+
 // Rows are processed in tiles of kBlock consecutive rows; CTAs stride over
 // tiles so that every CTA's partial sums have a fixed order.
 #define PRCG_ROWS(i, n)                                                         \
@@ -210,7 +225,7 @@ __global__ void __launch_bounds__(kBlock) k_hs_b(Op op, Pc pc, Vecs V, DevState*
 
 // Sweep C of iteration k: s_k = A p_k, mu_k = <p_k, s_k>; then alpha_k.
 template <class Op, class Pc>
-__global__ void __launch_bounds__(kBlock) k_hs_c(Op op, Pc pc, Vecs V, DevState* S,
+__global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value) k_hs_c(Op op, Pc pc, Vecs V, DevState* S,
                                                  double* partials) {
   if (__ldcg(&S->done)) return;
   double acc[1] = {0.0};
@@ -305,7 +320,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_a(Op op, Pc pc, Vecs V, DevState*
 // <r_k, r_k>, tests for convergence and forms alpha_k, nu'_{k+1} (Eq. 2.3
 // or Meurant's form), beta_{k+1}.
 template <class Op, class Pc>
-__global__ void __launch_bounds__(kBlock) k_pr_b(Op op, Pc pc, Vecs V, DevState* S,
+__global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value) k_pr_b(Op op, Pc pc, Vecs V, DevState* S,
                                                  double* partials, const double* partials_a,
                                                  int grid_a, int meurant) {
   if (__ldcg(&S->done)) return;

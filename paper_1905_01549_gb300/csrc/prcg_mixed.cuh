@@ -42,7 +42,8 @@ __device__ __forceinline__ float4 rows32x4(const StencilOp<DIM>& op, int i,
     return make_float4(op.row32(i, g), op.row32(i + 1, g), op.row32(i + 2, g), op.row32(i + 3, g));
   }
   const int nx = op.nx, ny = op.ny, nz = op.nz, pl = nx * ny;
-  const int x = i % nx, yz = i / nx, y = yz % ny, z = yz / ny;
+  int x, y, z;
+  op.coords(i, x, y, z);
   const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   auto ld4 = [&](int j) { return __ldg(reinterpret_cast<const float4*>(p + j)); };
   const float4 c = ld4(i);

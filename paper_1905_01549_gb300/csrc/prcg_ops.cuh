@@ -9,6 +9,7 @@
 #pragma once
 
 #include "prcg_common.cuh"
+#include "prcg_isum.cuh"
 
 namespace prcg {
 
@@ -39,6 +40,7 @@ struct OpDesc {
   int lda;               // dense: multiple of 32, >= n
   int ncb, cbw;          // dense: column blocks of the product and their width
   double* dpart[2];      // dense: partial products, [ncb][n] each
+  FastDiv divx, divy;    // stencils: division by nx and by ny
 };
 
 struct PcDesc {
@@ -144,21 +146,31 @@ struct SellOp {
 
 // ------------------------------------------- constant-coefficient stencil
 // 5-point (DIM 2) / 7-point (DIM 3) Poisson with Dirichlet-0 boundary:
-// y_i = cdiag * g(i) - sum over existing neighbours g(j).
+// y_i = cdiag * g(i) - sum over existing neighbours g(j).  The neighbour sum
+// is exact in fixed point (prcg_isum.cuh) and rounded once, so the FP64 pipe
+// -- the bottleneck of these sweeps on GB300 -- does one FMA per row instead
+// of 2*DIM+1; the result differs from a sequential FP64 evaluation only in
+// rounding (it is the more accurate of the two).
 template <int DIM>
 struct StencilOp {
   int nx, ny, nz, n;
   double cdiag;
-  explicit StencilOp(const OpDesc& o) : nx(o.nx), ny(o.ny), nz(o.nz), n(o.n), cdiag(o.cdiag) {}
+  FastDiv divx, divy;
+  explicit StencilOp(const OpDesc& o)
+      : nx(o.nx), ny(o.ny), nz(o.nz), n(o.n), cdiag(o.cdiag), divx(o.divx), divy(o.divy) {}
+  __device__ __forceinline__ void coords(int i, int& x, int& y, int& z) const {
+    const int yz = fast_div(divx, i);
+    x = i - yz * nx;
+    z = DIM == 3 ? fast_div(divy, yz) : 0;
+    y = yz - z * ny;
+  }
   // f(j, coefficient) for the 2*DIM+1 entries in increasing column order.
   // Missing neighbours (Dirichlet boundary) are visited as column i with
   // coefficient 0, so every load is issued unconditionally.
   template <class F>
   __device__ __forceinline__ void visit(int i, F&& f) const {
-    const int x = i % nx;
-    const int yz = i / nx;
-    const int y = yz % ny;
-    const int z = yz / ny;
+    int x, y, z;
+    coords(i, x, y, z);
     const int pl = nx * ny;
     if (DIM == 3) f(z > 0 ? i - pl : i, z > 0 ? -1.0 : 0.0);
     f(y > 0 ? i - nx : i, y > 0 ? -1.0 : 0.0);
@@ -168,14 +180,47 @@ struct StencilOp {
     f(y < ny - 1 ? i + nx : i, y < ny - 1 ? -1.0 : 0.0);
     if (DIM == 3) f(z < nz - 1 ? i + pl : i, z < nz - 1 ? -1.0 : 0.0);
   }
-  // one FMA chain per row: the large sweeps are bound by FP64 issue, so a
-  // second accumulator (one more FP64 add per row) would cost more than the
-  // chain latency it hides
+  // The 2*DIM neighbour values of row i (0 for a missing neighbour), every
+  // load issued unconditionally.
+  template <class G>
+  __device__ __forceinline__ void neighbours(int i, int x, int y, int z, G&& g,
+                                             double (&v)[2 * DIM]) const {
+    const int pl = nx * ny;
+    int t = 0;
+    if (DIM == 3) {
+      const double a = g(z > 0 ? i - pl : i);
+      v[t++] = z > 0 ? a : 0.0;
+    }
+    {
+      const double a = g(y > 0 ? i - nx : i);
+      v[t++] = y > 0 ? a : 0.0;
+    }
+    {
+      const double a = g(x > 0 ? i - 1 : i);
+      v[t++] = x > 0 ? a : 0.0;
+    }
+    {
+      const double a = g(x < nx - 1 ? i + 1 : i);
+      v[t++] = x < nx - 1 ? a : 0.0;
+    }
+    {
+      const double a = g(y < ny - 1 ? i + nx : i);
+      v[t++] = y < ny - 1 ? a : 0.0;
+    }
+    if (DIM == 3) {
+      const double a = g(z < nz - 1 ? i + pl : i);
+      v[t++] = z < nz - 1 ? a : 0.0;
+    }
+  }
+  // s_i = c p_i - sum of the neighbours: the sum on the integer pipes
+  // (exact, rounded once), one FP64 FMA per row
   template <class G>
   __device__ __forceinline__ double row(int i, G&& g) const {
-    double acc = 0.0;
-    visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
-    return acc;
+    int x, y, z;
+    coords(i, x, y, z);
+    double v[2 * DIM];
+    neighbours(i, x, y, z, g, v);
+    return fma(cdiag, g(i), -neighbour_sum<2 * DIM>(v));
   }
   template <class G>
   __device__ __forceinline__ float row32(int i, G&& g) const {
@@ -185,13 +230,13 @@ struct StencilOp {
   }
   template <class G1, class G2>
   __device__ __forceinline__ void row2(int i, G1&& g1, G2&& g2, double& a1, double& a2) const {
-    double c1 = 0.0, c2 = 0.0;
-    visit(i, [&](int j, double a) {
-      c1 = fma(a, g1(j), c1);
-      c2 = fma(a, g2(j), c2);
-    });
-    a1 = c1;
-    a2 = c2;
+    int x, y, z;
+    coords(i, x, y, z);
+    double v[2 * DIM];
+    neighbours(i, x, y, z, g1, v);
+    a1 = fma(cdiag, g1(i), -neighbour_sum<2 * DIM>(v));
+    neighbours(i, x, y, z, g2, v);
+    a2 = fma(cdiag, g2(i), -neighbour_sum<2 * DIM>(v));
   }
 };
 
@@ -204,14 +249,16 @@ struct VarStencilOp {
   const double* __restrict__ fy;
   const double* __restrict__ fz;
   const double* __restrict__ adiag;
+  FastDiv divx, divy;
   explicit VarStencilOp(const OpDesc& o)
-      : nx(o.nx), ny(o.ny), nz(o.nz), n(o.n), fx(o.fx), fy(o.fy), fz(o.fz), adiag(o.adiag) {}
+      : nx(o.nx), ny(o.ny), nz(o.nz), n(o.n), fx(o.fx), fy(o.fy), fz(o.fz), adiag(o.adiag),
+        divx(o.divx), divy(o.divy) {}
   template <class F>
   __device__ __forceinline__ void visit(int i, F&& f) const {
-    const int x = i % nx;
-    const int yz = i / nx;
-    const int y = yz % ny;
-    const int z = yz / ny;
+    const int yz = fast_div(divx, i);
+    const int x = i - yz * nx;
+    const int z = DIM == 3 ? fast_div(divy, yz) : 0;
+    const int y = yz - z * ny;
     const int pl = nx * ny;
     // face coefficients of the cell (boundary faces are valid addresses)
     const double czm = DIM == 3 ? __ldg(fz + i) : 0.0;
