@@ -435,20 +435,26 @@ def run_variants(G, prob, S_main, b_dev, args):
     return out
 
 
-def run_batched(G, args):
-    """512 shifted 2D Poisson systems (sides ~U{32..448}, shift ~U[0, 0.1],
-    b ~ U(-1, 1)) in one persistent launch to 1e-8; autotuned configuration.
-    Also the same systems one after another through prcg_solve."""
+def run_batched(G, args, count=512, config=None, plain=True):
+    """`count` (512) shifted 2D Poisson systems (sides ~U{32..448}, shift
+    ~U[0, 0.1], b ~ U(-1, 1)) in one persistent launch to 1e-8; autotuned
+    configuration unless `config` = (cluster, threads) is given.  With
+    `plain`, also the same systems one after another through prcg_solve."""
     import torch
     import problems as P
-    spec = P.batch_spec(512)
-    systems = [spec.system(i) for i in range(512)]
+    spec = P.batch_spec(count)
+    systems = [spec.system(i) for i in range(count)]
     nx = [s.dims[0] for s in systems]
     ny = [s.dims[1] for s in systems]
     B = G.BatchedSolver(nx, ny, spec.shifts)
     b = torch.from_numpy(np.concatenate([s.b for s in systems])).cuda()
     tol = 1e-8
-    cluster, threads, _, table = B.tune(b, tol=tol)
+    if config:
+        cluster, threads = config
+        B.configure(cluster, threads)
+        table = []
+    else:
+        cluster, threads, _, table = B.tune(b, tol=tol)
     ms = []
     for _ in range(max(2, args.steps)):
         x, iters, status, trr, worst, t = B.solve(b, tol=tol, true_relres=True)
@@ -463,8 +469,20 @@ def run_batched(G, args):
     sizes = np.array([x_ * y_ for x_, y_ in zip(nx, ny)], dtype=np.float64)
     row_iters = float((sizes * iters).sum())
     fp64 = 8.0 * row_iters
+    out = {"solves_per_s": count / (best / 1e3), "ms": best, "cluster": cluster,
+           "threads": threads, "systems": count,
+           "unknowns": int(sum(x_ * y_ for x_, y_ in zip(nx, ny))),
+           "iters_total": int(iters.sum()), "iters_max": int(iters.max()),
+           "all_converged": bool(np.all(status == 0)), "max_true_relres": float(trr.max()),
+           "row_iterations": row_iters,
+           "fp64_frac": fp64 / (best / 1e3) / fp64_peak(),
+           "fp64_model": "8 FP64 instructions per row-iteration (the 5-point neighbour sum "
+                         "runs on the integer pipes), peak 2 per SM per clock",
+           "tuning": table}
+    if not plain:
+        return out
     # plain path: the same systems, one prcg_solve each (every 4th system, scaled)
-    sel = list(range(0, 512, 4))
+    sel = list(range(0, count, 4))
     plain_ms = 0.0
     plain_iters = 0
     for i in sel:
@@ -476,18 +494,10 @@ def run_batched(G, args):
             plain_ms += r.init_ms + r.loop_ms
             plain_iters += r.iters
     plain_rate = len(sel) / (plain_ms / 1e3)
-    return {"solves_per_s": 512 / (best / 1e3), "ms": best, "cluster": cluster, "threads": threads,
-            "systems": 512, "unknowns": int(sum(x_ * y_ for x_, y_ in zip(nx, ny))),
-            "iters_total": int(iters.sum()), "iters_max": int(iters.max()),
-            "all_converged": bool(np.all(status == 0)), "max_true_relres": float(trr.max()),
-            "row_iterations": row_iters,
-            "fp64_frac": fp64 / (best / 1e3) / fp64_peak(),
-            "fp64_model": "8 FP64 instructions per row-iteration (the 5-point neighbour sum "
-                          "runs on the integer pipes), peak 2 per SM per clock",
-            "tuning": table,
-            "plain_fp64_path": {"solves_per_s": plain_rate,
-                                "sample": "every 4th system solved alone with prcg_solve "
-                                          "(device time of init + loop), rate over the sample"}}
+    out["plain_fp64_path"] = {"solves_per_s": plain_rate,
+                              "sample": "every 4th system solved alone with prcg_solve "
+                                        "(device time of init + loop), rate over the sample"}
+    return out
 
 
 def run_mixed(G, prob, args):
@@ -743,12 +753,22 @@ def main():
     ap.add_argument("--op", default="csr", choices=["csr", "stencil"])
     ap.add_argument("--variant", default="pr", choices=["pr", "hs", "pipe_pr", "m", "pipe_m"])
     ap.add_argument("--precond", default="jacobi", choices=["jacobi", "none"])
+    ap.add_argument("--batched-only", type=int, default=0, metavar="COUNT",
+                    help="time only the batched solver on COUNT systems (a profiling case)")
+    ap.add_argument("--batched-config", default="", metavar="CLUSTER,THREADS",
+                    help="with --batched-only: this launch configuration instead of the tuner")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     import __graft_entry__
     __graft_entry__.build()
+    if args.batched_only:
+        import paper_1905_01549_gb300 as G
+        cfg = tuple(int(v) for v in args.batched_config.split(",")) if args.batched_config else None
+        res = run_batched(G, args, count=args.batched_only, config=cfg, plain=False)
+        print(json.dumps({"batched": res}), flush=True)
+        return
     run_ours(args)
 
 
