@@ -115,6 +115,12 @@ int prcg_create_csr(prcg_ctx** out, int64_t n, int64_t nnz,
  *   diag_shift   added to the diagonal (>= 0 keeps A SPD)
  *   precond      prcg_precond
  * n = nx*ny*nz must be < 2^31.
+ * Arithmetic of the constant-coefficient product: (A v)_i = (2*dim + shift)
+ * v_i - S_i, where S_i, the sum of the existing neighbours, is formed exactly
+ * in 64-bit fixed point and rounded once (see prcg_test_neighbour_sum), then
+ * one FP64 FMA; it differs from an FP64 evaluation in the order of the
+ * stencil only in rounding, and is the more accurate of the two.  The
+ * variable-coefficient product is an FP64 FMA per entry.
  */
 int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t nz,
                         const double* face_coeff, double diag_shift, int precond,
