@@ -9,8 +9,46 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 
 namespace prcg {
+
+// Bit access used by the fixed-point sum, on the device through intrinsics
+// and on the host (tests) through memcpy and the compiler builtin.
+__host__ __device__ __forceinline__ unsigned isum_hi(double v) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__double2hiint(v);
+#else
+  uint64_t u;
+  std::memcpy(&u, &v, 8);
+  return (unsigned)(u >> 32);
+#endif
+}
+__host__ __device__ __forceinline__ unsigned isum_lo(double v) {
+#ifdef __CUDA_ARCH__
+  return (unsigned)__double2loint(v);
+#else
+  uint64_t u;
+  std::memcpy(&u, &v, 8);
+  return (unsigned)u;
+#endif
+}
+__host__ __device__ __forceinline__ double isum_from_bits(uint64_t u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double v;
+  std::memcpy(&v, &u, 8);
+  return v;
+#endif
+}
+__host__ __device__ __forceinline__ int isum_clz64(uint64_t a) {   // a != 0
+#ifdef __CUDA_ARCH__
+  return __clzll((long long)a);
+#else
+  return __builtin_clzll(a);
+#endif
+}
 
 // Division by an invariant divisor d >= 1 (Granlund and Montgomery,
 // "Division by invariant integers using multiplication", PLDI 1994, Fig. 4.1):
@@ -69,14 +107,15 @@ __host__ __device__ __forceinline__ int fast_div(const FastDiv& f, int n) {
 // at least 64 binades below the window and contribute nothing, which is
 // within the stated bound.
 template <int K>
-__device__ __forceinline__ bool fixed_point_sum(const double (&v)[K], double& out) {
+__host__ __device__ __forceinline__ bool fixed_point_sum(const double (&v)[K], double& out) {
   unsigned hi[K], lo[K];
   unsigned mx = 0;
 #pragma unroll
   for (int j = 0; j < K; ++j) {
-    hi[j] = (unsigned)__double2hiint(v[j]);
-    lo[j] = (unsigned)__double2loint(v[j]);
-    mx = max(mx, hi[j] & 0x7FFFFFFFu);
+    hi[j] = isum_hi(v[j]);
+    lo[j] = isum_lo(v[j]);
+    const unsigned mag = hi[j] & 0x7FFFFFFFu;
+    mx = mag > mx ? mag : mx;
   }
   const int E = (int)(mx >> 20);
   if (E < 64 || E > 2040) return false;
@@ -88,7 +127,8 @@ __device__ __forceinline__ bool fixed_point_sum(const double (&v)[K], double& ou
     const unsigned mh = (hi[j] & 0xFFFFFu) | 0x100000u;
     const uint64_t m = ((uint64_t)mh << 39) | ((uint64_t)lo[j] << 7);
     // a significand shifted by 63 is 0, so the shift is clamped there
-    const int d = min(E - (int)((hi[j] >> 20) & 0x7FFu), 63);
+    const int dd = E - (int)((hi[j] >> 20) & 0x7FFu);
+    const int d = dd < 63 ? dd : 63;
     acc += (long long)((m >> d) ^ (((uint64_t)sg << 32) | sg));
     neg -= (int)sg;
   }
@@ -100,7 +140,7 @@ __device__ __forceinline__ bool fixed_point_sum(const double (&v)[K], double& ou
   // |acc| < 2^63; the value is acc * 2^(E - 1082)
   const long long sm = acc >> 63;
   uint64_t a = (uint64_t)((acc ^ sm) - sm);
-  const int lz = __clzll((long long)a);
+  const int lz = isum_clz64(a);
   a <<= lz;
   uint64_t mant = a >> 11;   // 53 bits, the leading one at bit 52
   const unsigned rem = (unsigned)a & 0x7FFu;
@@ -108,7 +148,7 @@ __device__ __forceinline__ bool fixed_point_sum(const double (&v)[K], double& ou
   // biased exponent E + 4 - lz; adding the significand (leading one
   // included) to (exponent - 1) << 52 also carries a rounding overflow
   const uint64_t bits = ((uint64_t)(E + 3 - lz) << 52) + mant;
-  out = __longlong_as_double((long long)(bits | ((uint64_t)sm << 63)));
+  out = isum_from_bits(bits | ((uint64_t)sm << 63));
   return true;
 }
 
