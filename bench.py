@@ -455,6 +455,9 @@ def run_batched(G, args, count=512, config=None, plain=True):
         table = []
     else:
         cluster, threads, _, table = B.tune(b, tol=tol)
+    nbig, cluster_rest, threads_rest, clusters_rest = B.split()
+    split = ({"nbig": nbig, "cluster_rest": cluster_rest, "threads_rest": threads_rest,
+              "clusters_rest": clusters_rest} if nbig else None)
     ms = []
     for _ in range(max(2, args.steps)):
         x, iters, status, trr, worst, t = B.solve(b, tol=tol, true_relres=True)
@@ -470,7 +473,7 @@ def run_batched(G, args, count=512, config=None, plain=True):
     row_iters = float((sizes * iters).sum())
     fp64 = 8.0 * row_iters
     out = {"solves_per_s": count / (best / 1e3), "ms": best, "cluster": cluster,
-           "threads": threads, "systems": count,
+           "threads": threads, "split": split, "systems": count,
            "unknowns": int(sum(x_ * y_ for x_, y_ in zip(nx, ny))),
            "iters_total": int(iters.sum()), "iters_max": int(iters.max()),
            "all_converged": bool(np.all(status == 0)), "max_true_relres": float(trr.max()),

@@ -374,6 +374,18 @@ int prcg_batched_create(prcg_batch** out, int nsys, const int32_t* nx, const int
  * [64, 1024]; PRCG_ERR_UNSUPPORTED if the cluster cannot be resident. */
 int prcg_batched_configure(prcg_batch* bt, int cluster, int threads);
 
+/* Split launch: the nbig systems of largest estimated cost (1 <= nbig < nsys)
+ * are solved by one persistent launch with clusters of cluster_big CTAs x
+ * threads_big (one cluster per system, the first launch placed with the
+ * highest stream priority), the others by a second persistent launch of
+ * cluster_rest x threads_rest sized to the residency the first leaves free;
+ * the two run side by side in the solve's graph, each with its own work
+ * queue (no kernel waits on the other).  Large systems then get more SMs
+ * without slowing the many small ones.  Same limits as
+ * prcg_batched_configure; prcg_batched_configure returns to one launch. */
+int prcg_batched_configure_split(prcg_batch* bt, int nbig, int cluster_big, int threads_big,
+                                 int cluster_rest, int threads_rest);
+
 /* b, x: sum(n_i) doubles each, systems concatenated in creation order (host or
  * device); x holds x_0 on entry and x_K per system on return.  iters_out,
  * status_out (int32[nsys]) and true_relres_out (double[nsys], ||b - A x|| /
@@ -385,8 +397,14 @@ int prcg_batched_solve(prcg_batch* bt, const double* b, double* x, double tol, i
 /* device time (CUDA events) of the last batched solve's graph launch */
 int prcg_batched_last_ms(const prcg_batch* bt, float* ms);
 
-/* the launch configuration in use: cluster size, CTA size, resident clusters */
+/* the launch configuration in use: cluster size, CTA size, resident clusters
+ * (of the first launch when split) */
 int prcg_batched_config(const prcg_batch* bt, int* cluster, int* threads, int* clusters);
+
+/* the split in use: nbig and the second launch's cluster size, CTA size and
+ * clusters (all 0 for a single launch); any pointer may be NULL */
+int prcg_batched_split(const prcg_batch* bt, int* nbig, int* cluster_rest, int* threads_rest,
+                       int* clusters_rest);
 
 const char* prcg_batched_last_error(const prcg_batch* bt);
 

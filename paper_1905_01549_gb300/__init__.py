@@ -179,8 +179,17 @@ class BatchedSolver:
     def configure(self, cluster: int, threads: int):
         binding.prcg_batched_configure(self.handle, cluster, threads)
 
+    def configure_split(self, nbig: int, big, rest):
+        """The nbig costliest systems on clusters big = (cluster, threads),
+        the others on a concurrent launch of rest = (cluster, threads)."""
+        binding.prcg_batched_configure_split(self.handle, nbig, big[0], big[1], rest[0], rest[1])
+
     def config(self):
         return binding.prcg_batched_config(self.handle)
+
+    def split(self):
+        """(nbig, cluster, threads, clusters) of the second launch; zeros if not split."""
+        return binding.prcg_batched_split(self.handle)
 
     def tune(self, b, x0=None, tol: float = 1e-8, maxit: int = 100000, **kw):
         from . import autotune

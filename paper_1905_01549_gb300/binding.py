@@ -39,6 +39,7 @@ EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_create_dense", "prcg_
            "prcg_trace_enable", "prcg_trace_get", "prcg_check_guards",
            "prcg_inject_barrier_skip", "prcg_test_neighbour_sum",
            "prcg_pr_solve_stencil_noalloc", "prcg_batched_create", "prcg_batched_configure",
+           "prcg_batched_configure_split", "prcg_batched_split",
            "prcg_batched_solve", "prcg_batched_last_ms", "prcg_batched_config",
            "prcg_batched_last_error", "prcg_batched_destroy")
 
@@ -126,6 +127,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.prcg_batched_last_ms.restype = ctypes.c_int
     lib.prcg_batched_config.argtypes = [vp, _c_int_p, _c_int_p, _c_int_p]
     lib.prcg_batched_config.restype = ctypes.c_int
+    lib.prcg_batched_configure_split.argtypes = [vp] + [ctypes.c_int] * 5
+    lib.prcg_batched_configure_split.restype = ctypes.c_int
+    lib.prcg_batched_split.argtypes = [vp, _c_int_p, _c_int_p, _c_int_p, _c_int_p]
+    lib.prcg_batched_split.restype = ctypes.c_int
     lib.prcg_batched_last_error.argtypes = [vp]
     lib.prcg_batched_last_error.restype = ctypes.c_char_p
     lib.prcg_batched_destroy.argtypes = [vp]
@@ -347,6 +352,19 @@ def prcg_batched_create(nx, ny, shift, precond=PRCG_PRECOND_NONE, stream=None):
 
 def prcg_batched_configure(bt, cluster, threads):
     return _bcheck(load().prcg_batched_configure(bt, int(cluster), int(threads)), bt)
+
+
+def prcg_batched_configure_split(bt, nbig, cluster_big, threads_big, cluster_rest, threads_rest):
+    return _bcheck(load().prcg_batched_configure_split(bt, int(nbig), int(cluster_big),
+                                                       int(threads_big), int(cluster_rest),
+                                                       int(threads_rest)), bt)
+
+
+def prcg_batched_split(bt):
+    """(nbig, cluster_rest, threads_rest, clusters_rest); zeros for one launch."""
+    v = [ctypes.c_int() for _ in range(4)]
+    _bcheck(load().prcg_batched_split(bt, *[ctypes.byref(t) for t in v]), bt)
+    return tuple(t.value for t in v)
 
 
 def prcg_batched_solve(bt, b, x, tol, maxit, iters=None, status=None, true_relres=None):

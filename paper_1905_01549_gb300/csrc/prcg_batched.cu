@@ -302,6 +302,16 @@ struct prcg_batch {
   int cluster = 1;
   int threads = 256;
   int clusters = 0;
+  // Split launch (split > 0): the `split` systems of largest estimated cost
+  // run on clusters of cluster x threads, the others on a second,
+  // independent persistent launch of cluster2 x threads2 beside it (own work
+  // queue, forked and joined inside the same graph); 0: one launch.
+  int split = 0;
+  int cluster2 = 8;
+  int threads2 = 512;
+  int clusters2 = 0;
+  cudaStream_t cs2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t exec = nullptr;
   double graph_tol = -1.0;   // parameters the instantiated graph was captured with
   int graph_maxit = -1;
@@ -343,45 +353,78 @@ BatchArgs args_of(prcg_batch* bt, double tol, int maxit) {
   return a;
 }
 
-cudaError_t launch_batched(prcg_batch* bt, const BatchArgs& a, cudaStream_t st) {
+// One persistent launch of `clusters` clusters of `cluster` CTAs x `threads`;
+// `high_priority` asks the block scheduler to place its CTAs first.
+cudaError_t launch_batched(const BatchArgs& a, int cluster, int threads, int clusters,
+                           bool high_priority, cudaStream_t st) {
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof cfg);
-  cfg.gridDim = dim3(bt->clusters * bt->cluster);
-  cfg.blockDim = dim3(bt->threads);
+  cfg.gridDim = dim3(clusters * cluster);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
-  cudaLaunchAttribute at[1];
+  cudaLaunchAttribute at[2];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = bt->cluster;
+  at[0].val.clusterDim.x = cluster;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
+  if (high_priority) {
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess) {
+      at[1].id = cudaLaunchAttributePriority;
+      at[1].val.priority = greatest;
+      cfg.numAttrs = 2;
+    }
+  }
   return a.jacobi ? cudaLaunchKernelEx(&cfg, k_batched_pr<true>, a)
                   : cudaLaunchKernelEx(&cfg, k_batched_pr<false>, a);
 }
 
-// Persistent grid: as many clusters as can be resident at once.
-int size_grid(prcg_batch* bt) {
+// Clusters of `cluster` CTAs x `threads` that can be resident at once.
+int max_clusters(prcg_batch* bt, int cluster, int threads, int* nc) {
   const bool jac = bt->precond == PRCG_PRECOND_JACOBI;
   const void* kern = jac ? (const void*)k_batched_pr<true> : (const void*)k_batched_pr<false>;
-  if (bt->cluster > 8)
+  if (cluster > 8)
     BCK(cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof cfg);
-  cfg.gridDim = dim3(bt->cluster);
-  cfg.blockDim = dim3(bt->threads);
+  cfg.gridDim = dim3(cluster);
+  cfg.blockDim = dim3(threads);
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = bt->cluster;
+  at[0].val.clusterDim.x = cluster;
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  int nc = 0;
-  BCK(cudaOccupancyMaxActiveClusters(&nc, kern, &cfg));
-  if (nc < 1) return berr(bt, PRCG_ERR_UNSUPPORTED, "cluster configuration cannot be resident");
-  bt->clusters = std::min(nc, bt->nsys);
+  *nc = 0;
+  BCK(cudaOccupancyMaxActiveClusters(nc, kern, &cfg));
+  if (*nc < 1) return berr(bt, PRCG_ERR_UNSUPPORTED, "cluster configuration cannot be resident");
+  return PRCG_OK;
+}
+
+// Persistent grids: as many clusters as can be resident at once.  For a
+// split launch the first launch takes one cluster per large system (at most
+// what is resident) and the second what the first leaves free, counted in
+// CTA-thread slots, so that both run side by side.
+int size_grid(prcg_batch* bt) {
+  int nc = 0, rc = max_clusters(bt, bt->cluster, bt->threads, &nc);
+  if (rc != PRCG_OK) return rc;
+  if (bt->split <= 0) {
+    bt->clusters = std::min(nc, bt->nsys);
+    bt->clusters2 = 0;
+    return PRCG_OK;
+  }
+  bt->clusters = std::min(nc, bt->split);
+  int nc2 = 0;
+  if ((rc = max_clusters(bt, bt->cluster2, bt->threads2, &nc2)) != PRCG_OK) return rc;
+  const long long slots = (long long)nc2 * bt->cluster2 * bt->threads2;
+  const long long used = (long long)bt->clusters * bt->cluster * bt->threads;
+  const long long per = (long long)bt->cluster2 * bt->threads2;
+  const long long free_clusters = (slots - used) / per;
+  bt->clusters2 = (int)std::max(1LL, std::min<long long>(free_clusters, bt->nsys - bt->split));
   return PRCG_OK;
 }
 
@@ -432,13 +475,16 @@ int prcg_batched_create(prcg_batch** out, int nsys, const int32_t* nx, const int
   for (int i = 0; i < nsys; ++i) order[i] = i;
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   if (cudaStreamCreateWithFlags(&bt->cs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&bt->cs2, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&bt->ev_user, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&bt->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&bt->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreate(&bt->ev0) != cudaSuccess || cudaEventCreate(&bt->ev1) != cudaSuccess ||
       cudaMalloc(&bt->d_sys, nsys * sizeof(BatchSys)) != cudaSuccess ||
       cudaMalloc(&bt->d_order, nsys * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&bt->d_iters, nsys * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&bt->d_status, nsys * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&bt->d_queue, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&bt->d_queue, 2 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&bt->d_true, nsys * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&bt->pool, 6 * (size_t)off * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -461,13 +507,47 @@ int prcg_batched_configure(prcg_batch* bt, int cluster, int threads) {
     return berr(bt, PRCG_ERR_INVALID, "cluster must be 1, 2, 4, 8 or 16");
   if (threads < 64 || threads > kMaxThreads || threads % 32 != 0)
     return berr(bt, PRCG_ERR_INVALID, "threads must be a multiple of 32 in [64, 1024]");
-  const int oc = bt->cluster, ot = bt->threads;
+  const int oc = bt->cluster, ot = bt->threads, os = bt->split;
   bt->cluster = cluster;
   bt->threads = threads;
+  bt->split = 0;
   int rc = size_grid(bt);
   if (rc != PRCG_OK) {
     bt->cluster = oc;
     bt->threads = ot;
+    bt->split = os;
+    size_grid(bt);
+    return rc;
+  }
+  drop_graph(bt);
+  return PRCG_OK;
+}
+
+int prcg_batched_configure_split(prcg_batch* bt, int nbig, int cluster_big, int threads_big,
+                                 int cluster_rest, int threads_rest) {
+  if (!bt) return PRCG_ERR_INVALID;
+  if (nbig < 1 || nbig >= bt->nsys)
+    return berr(bt, PRCG_ERR_INVALID, "nbig must be in [1, number of systems)");
+  for (int c : {cluster_big, cluster_rest})
+    if (c < 1 || c > 16 || (c & (c - 1)) != 0)
+      return berr(bt, PRCG_ERR_INVALID, "cluster must be 1, 2, 4, 8 or 16");
+  for (int t : {threads_big, threads_rest})
+    if (t < 64 || t > kMaxThreads || t % 32 != 0)
+      return berr(bt, PRCG_ERR_INVALID, "threads must be a multiple of 32 in [64, 1024]");
+  const int oc = bt->cluster, ot = bt->threads, os = bt->split, oc2 = bt->cluster2,
+            ot2 = bt->threads2;
+  bt->cluster = cluster_big;
+  bt->threads = threads_big;
+  bt->split = nbig;
+  bt->cluster2 = cluster_rest;
+  bt->threads2 = threads_rest;
+  int rc = size_grid(bt);
+  if (rc != PRCG_OK) {
+    bt->cluster = oc;
+    bt->threads = ot;
+    bt->split = os;
+    bt->cluster2 = oc2;
+    bt->threads2 = ot2;
     size_grid(bt);
     return rc;
   }
@@ -485,13 +565,30 @@ int prcg_batched_solve(prcg_batch* bt, const double* b, double* x, double tol, i
   BCK(cudaStreamWaitEvent(bt->cs, bt->ev_user, 0));
   BCK(cudaMemcpyAsync((void*)a.b, b, bytes, cudaMemcpyDefault, bt->cs));
   BCK(cudaMemcpyAsync(a.x, x, bytes, cudaMemcpyDefault, bt->cs));
-  // one graph: reset the work queue, the persistent solver launch
+  // one graph: reset the work queues, the persistent solver launch (or, for
+  // a split, the two launches forked onto two streams and joined again)
   if (bt->exec && (bt->graph_tol != tol || bt->graph_maxit != maxit)) drop_graph(bt);
   if (!bt->exec) {
     cudaGraph_t g = nullptr;
     BCK(cudaStreamBeginCapture(bt->cs, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = cudaMemsetAsync(bt->d_queue, 0, sizeof(int), bt->cs);
-    if (e == cudaSuccess) e = launch_batched(bt, a, bt->cs);
+    cudaError_t e = cudaMemsetAsync(bt->d_queue, 0, 2 * sizeof(int), bt->cs);
+    if (bt->split <= 0) {
+      if (e == cudaSuccess) e = launch_batched(a, bt->cluster, bt->threads, bt->clusters, false, bt->cs);
+    } else {
+      BatchArgs big = a, rest = a;
+      big.nsys = bt->split;
+      rest.order = bt->d_order + bt->split;
+      rest.nsys = bt->nsys - bt->split;
+      rest.queue = bt->d_queue + 1;
+      if (e == cudaSuccess) e = cudaEventRecord(bt->ev_fork, bt->cs);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->cs2, bt->ev_fork, 0);
+      if (e == cudaSuccess)
+        e = launch_batched(big, bt->cluster, bt->threads, bt->clusters, true, bt->cs);
+      if (e == cudaSuccess)
+        e = launch_batched(rest, bt->cluster2, bt->threads2, bt->clusters2, false, bt->cs2);
+      if (e == cudaSuccess) e = cudaEventRecord(bt->ev_join, bt->cs2);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(bt->cs, bt->ev_join, 0);
+    }
     cudaError_t e2 = cudaStreamEndCapture(bt->cs, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
       if (g) cudaGraphDestroy(g);
@@ -546,6 +643,17 @@ int prcg_batched_config(const prcg_batch* bt, int* cluster, int* threads, int* c
   return PRCG_OK;
 }
 
+int prcg_batched_split(const prcg_batch* bt, int* nbig, int* cluster_rest, int* threads_rest,
+                       int* clusters_rest) {
+  if (!bt) return PRCG_ERR_INVALID;
+  const bool on = bt->split > 0;
+  if (nbig) *nbig = on ? bt->split : 0;
+  if (cluster_rest) *cluster_rest = on ? bt->cluster2 : 0;
+  if (threads_rest) *threads_rest = on ? bt->threads2 : 0;
+  if (clusters_rest) *clusters_rest = on ? bt->clusters2 : 0;
+  return PRCG_OK;
+}
+
 const char* prcg_batched_last_error(const prcg_batch* bt) { return bt ? bt->err.c_str() : ""; }
 
 int prcg_batched_destroy(prcg_batch* bt) {
@@ -562,6 +670,9 @@ int prcg_batched_destroy(prcg_batch* bt) {
   if (bt->ev_user) cudaEventDestroy(bt->ev_user);
   if (bt->ev0) cudaEventDestroy(bt->ev0);
   if (bt->ev1) cudaEventDestroy(bt->ev1);
+  if (bt->ev_fork) cudaEventDestroy(bt->ev_fork);
+  if (bt->ev_join) cudaEventDestroy(bt->ev_join);
+  if (bt->cs2) cudaStreamDestroy(bt->cs2);
   if (bt->cs) cudaStreamDestroy(bt->cs);
   delete bt;
   return PRCG_OK;

@@ -72,6 +72,39 @@ def test_batched_matches_single_system_oracle(G, precond):
     B.close()
 
 
+@pytest.mark.parametrize("precond", ["none", "jacobi"])
+def test_split_launch_matches_single_system_oracle(G, precond):
+    """The costliest systems on one launch, the rest on a concurrent second
+    launch: every system still matches its own oracle solve."""
+    import torch
+    systems = _batch()
+    B = G.BatchedSolver([s.dims[0] for s in systems], [s.dims[1] for s in systems],
+                        [s.shift for s in systems], precond=precond)
+    b = torch.from_numpy(np.concatenate([s.b for s in systems])).cuda()
+    refs = [_oracle(s, precond) for s in systems]
+    for nbig, big, rest in [(3, (16, 256), (4, 128)), (6, (8, 512), (1, 256)),
+                            (23, (2, 64), (1, 64))]:
+        B.configure_split(nbig, big, rest)
+        assert B.split()[:3] == (nbig,) + rest and B.config()[:2] == big
+        x, iters, status, trr, worst, ms = B.solve(b, tol=TOL, true_relres=True)
+        assert worst == G.PRCG_OK and np.all(status == 0), (nbig, big, rest)
+        xs = x.cpu().numpy()
+        for i, (s, (A, ref)) in enumerate(zip(systems, refs)):
+            xi = xs[B.offsets[i]:B.offsets[i + 1]]
+            assert abs(int(iters[i]) - ref.iters) <= max(1, 0.05 * ref.iters), (i, iters[i])
+            assert rel(xi, ref.x) <= 1e-6 and trr[i] <= 2 * TOL, i
+        x2, *_ = B.solve(b, tol=TOL)
+        assert np.array_equal(x2.cpu().numpy(), xs)
+    B.configure(1, 256)
+    assert B.split() == (0, 0, 0, 0)
+    from paper_1905_01549_gb300 import binding
+    for nbig in (0, len(systems)):
+        with pytest.raises(binding.PrcgError):
+            B.configure_split(nbig, (8, 256), (1, 256))
+    assert B.config()[:2] == (1, 256) and B.split()[0] == 0   # a refused split changes nothing
+    B.close()
+
+
 def test_batched_zero_rhs_maxit_and_host_buffers(G):
     import torch
     systems = _batch(6)
@@ -101,7 +134,8 @@ def test_autotuner_picks_and_caches(G, tmp_path):
                         [s.shift for s in systems])
     b = torch.from_numpy(np.concatenate([s.b for s in systems])).cuda()
     cache = str(tmp_path / "tune.json")
-    c, t, ms, table = B.tune(b, cache_path=cache, candidates=((1, 256), (2, 256), (4, 128)))
+    c, t, ms, table = B.tune(b, cache_path=cache, candidates=((1, 256), (2, 256), (4, 128)),
+                             splits=())
     assert (c, t) in [(1, 256), (2, 256), (4, 128)] and ms > 0
     assert B.config()[:2] == (c, t)
     B.configure(1, 64)

@@ -29,6 +29,12 @@ class _FakeBatched:
             raise self.binding.PrcgError(self.binding.PRCG_ERR_UNSUPPORTED, "not resident")
         self.cfg = (cluster, threads)
 
+    def configure_split(self, bt, nbig, cb, tb, cr, tr):
+        key = (nbig, cb, tb, cr, tr)
+        if key in self.refuse or key not in self.times:
+            raise self.binding.PrcgError(self.binding.PRCG_ERR_INVALID, "no such split")
+        self.cfg = key
+
     def solve(self, bt, b, x, tol, maxit, *args):
         self.solves += 1
         x.fill_(1.0)
@@ -40,6 +46,7 @@ class _FakeBatched:
 
 def _install(monkeypatch, autotune, fake):
     monkeypatch.setattr(autotune.binding, "prcg_batched_configure", fake.configure)
+    monkeypatch.setattr(autotune.binding, "prcg_batched_configure_split", fake.configure_split)
     monkeypatch.setattr(autotune.binding, "prcg_batched_solve", fake.solve)
     monkeypatch.setattr(autotune.binding, "prcg_batched_last_ms", fake.last_ms)
 
@@ -67,6 +74,29 @@ def test_tuner_picks_fastest_skips_unlaunchable_and_caches(G, monkeypatch, tmp_p
     assert fake.solves == n_solves                           # answered from the cache
 
 
+def test_tuner_picks_and_caches_a_split_launch(G, monkeypatch, tmp_path):
+    import torch
+    from paper_1905_01549_gb300 import autotune
+    cands = [(8, 512), (16, 512)]
+    splits = [(4, 16, 512, 8, 512), (8, 16, 512, 8, 512), (600, 16, 512, 8, 512)]
+    times = {(8, 512): 3.0, (16, 512): 4.0, (4, 16, 512, 8, 512): 2.0,
+             (8, 16, 512, 8, 512): 2.4}
+    fake = _FakeBatched(autotune.binding, times)
+    _install(monkeypatch, autotune, fake)
+    cache = str(tmp_path / "tune.json")
+    x0 = torch.zeros(10, dtype=torch.float64)
+    key = autotune.batch_key([32, 448], [40, 448], [0.0, 0.05], 0, 1e-8, "dev")
+    c, t, ms, table = autotune.tune(None, None, x0, 1e-8, 100, key=key, candidates=cands,
+                                    splits=splits, cache_path=cache)
+    assert (c, t, ms) == (16, 512, 2.0) and fake.cfg == (4, 16, 512, 8, 512)
+    assert (600, 16, 512, 8, 512, None) in [tuple(r) for r in table]   # rejected: recorded
+    n_solves = fake.solves
+    fake.cfg = None
+    autotune.tune(None, None, x0, 1e-8, 100, key=key, candidates=cands, splits=splits,
+                  cache_path=cache)
+    assert fake.cfg == (4, 16, 512, 8, 512) and fake.solves == n_solves   # split re-applied
+
+
 def test_tuner_fails_loudly_when_nothing_launches(G, monkeypatch, tmp_path):
     import torch
     from paper_1905_01549_gb300 import autotune
@@ -74,7 +104,8 @@ def test_tuner_fails_loudly_when_nothing_launches(G, monkeypatch, tmp_path):
     _install(monkeypatch, autotune, fake)
     with pytest.raises(RuntimeError):
         autotune.tune(None, None, torch.zeros(4, dtype=torch.float64), 1e-8, 10,
-                      candidates=[(1, 256), (2, 256)], cache_path=str(tmp_path / "t.json"))
+                      candidates=[(1, 256), (2, 256)], splits=[(2, 16, 512, 8, 512)],
+                      cache_path=str(tmp_path / "t.json"))
 
 
 def test_tuning_key_separates_what_changes_the_choice(G):
