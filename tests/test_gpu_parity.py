@@ -261,6 +261,31 @@ def test_nan_in_b_reports_breakdown_and_context_recovers(G, torch_mod, path, mon
 
 
 @pytest.mark.parametrize("path", ["persistent", "graph"])
+@pytest.mark.parametrize("name", ["poisson3d_ragged", "shifted2d"])
+def test_point_source_mixes_fallback_and_fixed_point_rows(G, torch_mod, name, path, monkeypatch):
+    """b = a point source: for the first iterations most rows of p see only
+    exact zeros (the stencil's neighbour sum then takes its FP64 fallback)
+    next to rows in the fixed-point window; the iterates still match the
+    oracle element by element."""
+    torch = torch_mod
+    if path == "graph":
+        monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    prob = case(name)
+    A = csr_matrix(prob)
+    b = np.zeros(prob.n)
+    b[prob.n // 3] = 1.0
+    with make_solver(G, prob, "stencil", "none") as S:
+        for variant in ("hs", "pr", "pipe_pr"):
+            for k in (1, 3, 8, 20):
+                res = S.solve(torch.from_numpy(b).cuda(), variant=variant, tol=0.0, maxit=k,
+                              history=True)
+                ref, sx, sh = oracle_spread(variant, A, b, None, k)
+                assert res.iters == ref.iters == k, (variant, k)
+                tol_x = max(ITER_TOL, SPREAD_FACTOR * sx)
+                assert rel(res.x.cpu().numpy(), ref.x) <= tol_x, (variant, k, tol_x)
+
+
+@pytest.mark.parametrize("path", ["persistent", "graph"])
 def test_exact_initial_guess_stops_at_zero_iterations(G, torch_mod, path, monkeypatch):
     """x_0 = A^{-1} b exactly (integer x_0, integer stencil, so b = A x_0 and
     r_0 = 0 in floating point): every variant returns OK with K = 0 and x_0."""
