@@ -37,6 +37,22 @@ struct SweepMinBlocks<StencilOp<DIM>> {
   static constexpr int value = 8;
 };
 
+// t - alpha (M^{-1} v)_i: the update of a recurrence for a preconditioned
+// vector (r~ of PR-CG, w~' of pipe-PR-CG).  For a Jacobi vector d it forms
+// the explicit d_i v_i of the algorithm and one FMA; for a constant d the
+// caller passes ad = alpha d, formed once per sweep, and the update is one
+// FMA -- the same quantity reassociated, one FP64 instruction less per row
+// on the FP64-starved sweeps (the constant d is likewise factored out of the
+// inner products <r, r~> and <s, s~>).
+template <class Pc>
+__device__ __forceinline__ double sub_scaled(const Pc& pc, int i, double alpha, double ad,
+                                             double v, double t) {
+  if constexpr (std::is_same<Pc, PcScalar>::value)
+    return fma(-ad, v, t);
+  else
+    return fma(-alpha, pc(i) * v, t);
+}
+
 // Rows are processed in tiles of kBlock consecutive rows; CTAs stride over
 // tiles so that every CTA's partial sums have a fixed order.
 #define PRCG_ROWS(i, n)                                                         \
@@ -225,8 +241,8 @@ __global__ void __launch_bounds__(kBlock) k_hs_b(Op op, Pc pc, Vecs V, DevState*
 
 // Sweep C of iteration k: s_k = A p_k, mu_k = <p_k, s_k>; then alpha_k.
 template <class Op, class Pc>
-__global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value) k_hs_c(Op op, Pc pc, Vecs V, DevState* S,
-                                                 double* partials) {
+__global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
+    k_hs_c(Op op, Pc pc, Vecs V, DevState* S, double* partials) {
   if (__ldcg(&S->done)) return;
   double acc[1] = {0.0};
   const double* __restrict__ p = V.p[0];
@@ -260,6 +276,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_a(Op op, Pc pc, Vecs V, DevState*
   if (__ldcg(&S->done)) return;
   const double alpha = __ldcg(&S->alpha);
   const double beta = __ldcg(&S->beta);
+  const double ad = std::is_same<Pc, PcScalar>::value ? alpha * pc(0) : 0.0;
   double* __restrict__ x = V.x;
   double* __restrict__ r = V.r[0];
   double* __restrict__ rt = V.rt[0];
@@ -273,7 +290,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_a(Op op, Pc pc, Vecs V, DevState*
     ri = rn;
     double rtn = rn;
     if (Pc::on) {
-      rtn = fma(-alpha, di * si, rti);
+      rtn = std::is_same<Pc, PcScalar>::value ? fma(-ad, si, rti) : fma(-alpha, di * si, rti);
       rti = rtn;
       acc[0] = fma(rtn, rn, acc[0]);
     }
@@ -320,9 +337,9 @@ __global__ void __launch_bounds__(kBlock) k_pr_a(Op op, Pc pc, Vecs V, DevState*
 // <r_k, r_k>, tests for convergence and forms alpha_k, nu'_{k+1} (Eq. 2.3
 // or Meurant's form), beta_{k+1}.
 template <class Op, class Pc>
-__global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value) k_pr_b(Op op, Pc pc, Vecs V, DevState* S,
-                                                 double* partials, const double* partials_a,
-                                                 int grid_a, int meurant) {
+__global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
+    k_pr_b(Op op, Pc pc, Vecs V, DevState* S, double* partials, const double* partials_a,
+           int grid_a, int meurant) {
   if (__ldcg(&S->done)) return;
   const double* __restrict__ p = V.p[0];
   const double* __restrict__ rt = Pc::on ? V.rt[0] : V.r[0];
@@ -376,6 +393,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
   if (__ldcg(&S->done)) return;
   const double alpha = __ldcg(&S->alpha);
   const double beta = __ldcg(&S->beta);
+  const double ad = std::is_same<Pc, PcScalar>::value ? alpha * pc(0) : 0.0;
   const double* __restrict__ rt_o = Pc::on ? V.rt[qr] : V.r[qr];
   const double* __restrict__ st_o = Pc::on ? V.st[qr] : V.s[qr];
   const double* __restrict__ r_o = V.r[qr];
@@ -396,7 +414,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
       const double di = pc(i);
       const double sti = __ldg(st_o + i);
       rtn = fma(-alpha, sti, __ldg(rt_o + i));
-      const double wtp = fma(-alpha, di * u, di * w);
+      const double wtp = sub_scaled(pc, i, alpha, ad, u, di * w);
       sn = fma(beta, si, wp);
       stn = fma(beta, sti, wtp);
       V.rt[qw][i] = rtn;
@@ -449,6 +467,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe_nr(Op op, Pc pc, Vecs V, DevSta
   double* __restrict__ p = V.p[0];
   double* __restrict__ w = V.w[0];
   double* __restrict__ wt = V.u[0];
+  const double ad = std::is_same<Pc, PcScalar>::value ? alpha * pc(0) : 0.0;
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   PRCG_ROWS(i, op.n) {
     const double u = op.row(i, [&](int j) { return __ldg(st_o + j); });
@@ -461,7 +480,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe_nr(Op op, Pc pc, Vecs V, DevSta
     if (Pc::on) {
       const double sti = __ldg(st_o + i);
       rtn = fma(-alpha, sti, __ldg(rt_o + i));
-      const double wtp = fma(-alpha, pc(i) * u, wt[i]);
+      const double wtp = sub_scaled(pc, i, alpha, ad, u, wt[i]);
       wt[i] = wtp;
       sn = fma(beta, si, wp);
       stn = fma(beta, sti, wtp);

@@ -460,6 +460,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
     } else if (VARIANT == V_PR) {
       // A: x_k, r_k, r~_k, p_k; partial nu_k, rho_k
       double a5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      const double ad = std::is_same<Pc, PcScalar>::value ? alpha * pc(0) : 0.0;
       PRCG_OWN_ROWS(i, rb) {
         const double si = V.s[0][i], pi = V.p[0][i];
         x[i] = fma(alpha, pi, x[i]);
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         V.r[0][i] = rn;
         double rtn = rn;
         if (Pc::on) {
-          rtn = fma(-alpha, pc(i) * si, V.rt[0][i]);
+          rtn = sub_scaled(pc, i, alpha, ad, si, V.rt[0][i]);
           V.rt[0][i] = rtn;
         }
         V.p[0][i] = fma(beta, pi, rtn);
@@ -524,6 +525,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         return;
       }
       double a5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      const double ad = std::is_same<Pc, PcScalar>::value ? alpha * pc(0) : 0.0;
       PRCG_OWN_ROWS(i, rb) {
         double u, w;
         op.row2(i, [&](int j) { return __ldcg(st_o + j); }, [&](int j) { return __ldcg(rt_o + j); },
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
           const double di = pc(i);
           const double sti = st_o[i];
           rtn = fma(-alpha, sti, rt_o[i]);
-          const double wtp = fma(-alpha, di * u, di * w);
+          const double wtp = sub_scaled(pc, i, alpha, ad, u, di * w);
           sn = fma(beta, si, wp);
           stn = fma(beta, sti, wtp);
           V.rt[qw][i] = rtn;
