@@ -572,15 +572,14 @@ def run_autograd(G, args):
             "grad_norm_b": float(bc.grad.norm())}
 
 
-# Table 2, row model_48_8_3, as printed in the paper (iterations to a 10^5
-# A-norm error reduction, min log10 error); the paper's eigenvector draw is
-# not known, so these are context, not expected values.
-PAPER_TABLE2_MODEL_48_8_3 = {
-    "none": {"hs": (43, -14.32), "cgcg": (42, -14.28), "m": (45, -14.31), "pr": (44, -14.32),
-             "gv": (45, -10.23), "pipe_m": (43, -13.67), "pipe_pr": (44, -13.66)},
-    "jacobi": {"hs": (49, -14.30), "cgcg": (48, -14.25), "m": (50, -14.28), "pr": (50, -14.29),
-               "gv": (52, -10.66), "pipe_m": (50, -13.70), "pipe_pr": (50, -13.72)},
-}
+def paper_table2_model_48_8_3():
+    """Table 2, row model_48_8_3, as printed in the paper (iterations to a
+    10^5 A-norm error reduction, min log10 error), read from the fixture
+    tests/golden/table2_model_48_8_3.txt; the paper's eigenvector draw is not
+    known, so these are context, not expected values."""
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from golden import table2
+    return table2()
 
 
 def run_convergence(G, args):
@@ -598,12 +597,13 @@ def run_convergence(G, args):
     xs = torch.from_numpy(prob.x_star).cuda()
     out = {"workload": "model_48_8_3 (Eq. 4.1, Haar eigenvectors from the seeded generator), k <= 200"}
     t0 = time.perf_counter()
+    paper = paper_table2_model_48_8_3()
     for pc in ("none", "jacobi"):
         with G.Solver.from_csr(rp, ci, np.ascontiguousarray(prob.A.ravel()), precond=pc) as S:
             st = convergence.study(S, b, xs, ["hs", "cgcg", "m", "pr", "gv", "pipe_m", "pipe_pr"], 200)
         out[pc] = {v: {"iters_to_1e5": r["iters_to_reduction"],
                        "min_log10_err": round(r["min_log10_err"], 2),
-                       "paper": PAPER_TABLE2_MODEL_48_8_3[pc][v]} for v, r in st.items()}
+                       "paper": paper[pc][v]} for v, r in st.items()}
     out["seconds"] = round(time.perf_counter() - t0, 2)
     return out
 

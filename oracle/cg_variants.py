@@ -200,8 +200,10 @@ def initialize(run: _Run, x0, need_pipe: bool):
 
 
 def _gap_tracks(run, k, x, r, st=None, w=None):
+    """Record tracked quantities; `st` is a callable, evaluated only when the
+    nu'-gap is tracked (its <r, r> is not part of the iteration's work)."""
     if "nu_gap" in run.track and st is not None:
-        run.extra["nu_gap"].append((k, st))
+        run.extra["nu_gap"].append((k, st()))
     if "w_gap" in run.track and w is not None:
         run.extra["w_gap"].append((k, w))
 
@@ -281,14 +283,17 @@ def pr_cg(A, b, x0=None, d=None, tol=0.0, maxit=None, record=0, track=None,
         st = run.Minv(s)                                           # s~_k = M^{-1} s_k
         # the inner products, all in one reduction
         mu = _dot(p, s)                                            # mu_k
-        sigma = _dot(rt, s)                                        # sigma_k
+        if not meurant:   # Meurant's nu' (Appendix E) reads no sigma
+            sigma = _dot(rt, s)                                        # sigma_k
         gamma = _dot(st, s)                                        # gamma_k
         nu_true = _dot(rt, r)                                      # nu_k (recomputed)
         rho = nu_true if run.d is None else _dot(r, r)
         nu = nu_true if recompute_nu else nu_pred
         run.scalars.append(dict(alpha=alpha, beta=beta, nu_pred=nu_pred, nu=nu_true,
                                 mu=mu, sigma=sigma, gamma=gamma, rho=rho))
-        _gap_tracks(run, k, x, r, st=(nu_pred, _dot(r, r)))
+        if meurant:
+            del run.scalars[-1]["sigma"]
+        _gap_tracks(run, k, x, r, st=lambda: (nu_pred, _dot(r, r)))
         if run.log(k, x, r, rho):
             return run.result(x, k, OK)
     return run.result(x, run.maxit, NOT_CONVERGED)
@@ -344,14 +349,17 @@ def pipe_pr_cg(A, b, x0=None, d=None, tol=0.0, maxit=None, record=0, track=None,
         else:
             w, wt = wp, wtp
         mu = _dot(p, s)
-        sigma = _dot(rt, s)
+        if not meurant:   # Meurant's nu' (Appendix E) reads no sigma
+            sigma = _dot(rt, s)
         gamma = _dot(st, s)
         nu_true = _dot(rt, r)
         rho = nu_true if not pc else _dot(r, r)
         nu = nu_true
         run.scalars.append(dict(alpha=alpha, beta=beta, nu_pred=nu_pred, nu=nu_true,
                                 mu=mu, sigma=sigma, gamma=gamma, rho=rho))
-        _gap_tracks(run, k, x, r, st=(nu_pred, _dot(r, r)), w=(r, wp))
+        if meurant:
+            del run.scalars[-1]["sigma"]
+        _gap_tracks(run, k, x, r, st=lambda: (nu_pred, _dot(r, r)), w=(r, wp))
         if run.log(k, x, r, rho):
             return run.result(x, k, OK)
     return run.result(x, run.maxit, NOT_CONVERGED)
