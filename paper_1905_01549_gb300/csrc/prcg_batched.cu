@@ -90,7 +90,8 @@ static __device__ __noinline__ double sequential_sum4(double a, double b, double
 // (A v)_i = cdiag v_i - sum of the existing neighbours; the neighbour sum is
 // exact in fixed point on the integer pipes and rounded once
 // (prcg_isum.cuh), leaving one FP64 FMA per row.
-__device__ __forceinline__ double stencil_row(const BatchSys& q, const double* __restrict__ v, int i) {
+__device__ __forceinline__ double stencil_row(const BatchSys& q, const double* __restrict__ v,
+                                              int i) {
   const int y = prcg::fast_div(q.divx, i), x = i - y * q.nx;
   const double ym = __ldcg(v + (y > 0 ? i - q.nx : i));
   const double xm = __ldcg(v + (x > 0 ? i - 1 : i));
@@ -573,7 +574,8 @@ int prcg_batched_solve(prcg_batch* bt, const double* b, double* x, double tol, i
     BCK(cudaStreamBeginCapture(bt->cs, cudaStreamCaptureModeThreadLocal));
     cudaError_t e = cudaMemsetAsync(bt->d_queue, 0, 2 * sizeof(int), bt->cs);
     if (bt->split <= 0) {
-      if (e == cudaSuccess) e = launch_batched(a, bt->cluster, bt->threads, bt->clusters, false, bt->cs);
+      if (e == cudaSuccess)
+        e = launch_batched(a, bt->cluster, bt->threads, bt->clusters, false, bt->cs);
     } else {
       BatchArgs big = a, rest = a;
       big.nsys = bt->split;
