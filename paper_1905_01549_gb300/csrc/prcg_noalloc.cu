@@ -19,6 +19,7 @@
 // serialise them.  Each call rewrites all scratch it reads before reading it.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 
 #include "../../include/prcg.h"
@@ -30,13 +31,21 @@ constexpr int kNoallocMaxN = 65536;       // largest n the scratch holds
 constexpr int kNoallocThreads = 1024;
 constexpr int kNoallocVectors = 8;        // r, r~, p, s, each double-buffered
 constexpr int kHeaderDoubles = 32;
+// The solve is one kernel that cannot be interrupted; maxit is bounded so
+// that a tolerance the system cannot reach ends in bounded time.
+constexpr int64_t kNoallocMaxItPerRow = 4;
+constexpr int64_t kNoallocMaxItExtra = 1000;
+constexpr int kMaxDevices = 64;
 
 // file-scope scratch: [header][8 vectors of kNoallocMaxN doubles]
 static __device__ __align__(256) double g_noalloc_scratch[kHeaderDoubles +
                                                           kNoallocVectors * kNoallocMaxN];
 
-int g_scratch_device_ready[64];           // 1 once the address of this device is known
-double* g_scratch_ptr[64];
+// Device address of the scratch array per device, null until the first call
+// on that device looks it up.  Several host threads may make their first
+// call at once: each then stores the same address, which the symbol lookup
+// returns for that device every time.
+std::atomic<double*> g_scratch_ptr[kMaxDevices];
 
 struct NoallocArgs {
   int dim, nx, ny, nz, n;
@@ -102,7 +111,9 @@ k_pr_noalloc(NoallocArgs a, double* scratch) {
   if (tid == 0) {
     st_nu = acc3[0];
     st_bn2 = acc3[2];
-    double rel = acc3[2] > 0.0 ? sqrt(acc3[1]) / sqrt(acc3[2]) : 0.0;
+    // b == 0 counts as converged; a non-finite ||b|| stays non-finite, so the
+    // stopping test fails and the scalar step reports the breakdown
+    double rel = acc3[2] != 0.0 ? sqrt(acc3[1]) / sqrt(acc3[2]) : 0.0;
     if (a.hist) a.hist[0] = rel;
     int status = -100;
     if (acc3[2] == 0.0 || rel <= a.tol) status = 0;
@@ -220,29 +231,31 @@ k_pr_noalloc(NoallocArgs a, double* scratch) {
 
 // Device address of the scratch array for the current device (set-up on the
 // first call per device).
-int scratch_for_device(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PRCG_ERR_CUDA;
-  if (!g_scratch_device_ready[dev]) {
-    double* ptr = nullptr;
+int scratch_for_device(int dev, double** out) {
+  if (dev < 0 || dev >= kMaxDevices) return PRCG_ERR_CUDA;
+  double* ptr = g_scratch_ptr[dev].load(std::memory_order_acquire);
+  if (!ptr) {
     if (cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
       cudaGetLastError();
       return PRCG_ERR_CUDA;
     }
-    g_scratch_ptr[dev] = ptr;
-    g_scratch_device_ready[dev] = 1;
+    g_scratch_ptr[dev].store(ptr, std::memory_order_release);
   }
-  *out = g_scratch_ptr[dev];
+  *out = ptr;
   return PRCG_OK;
 }
 
-bool is_device_pointer(const void* p) {
+// True for memory the kernel on device `dev` may dereference: device memory
+// of `dev` itself, or managed memory.  Device memory of another GPU is
+// refused (without peer access a load from it would fault).
+bool is_device_pointer(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return true;
+  return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 }  // namespace
@@ -255,15 +268,24 @@ extern "C" int prcg_pr_solve_stencil_noalloc(int dim, int64_t nx, int64_t ny, in
   if (dim != 2 && dim != 3) return PRCG_ERR_INVALID;
   if (dim == 2) nz = 1;
   if (nx < 1 || ny < 1 || nz < 1) return PRCG_ERR_INVALID;
+  // each extent is bounded before the product is formed, so it cannot overflow
+  if (nx > kNoallocMaxN || ny > kNoallocMaxN || nz > kNoallocMaxN) return PRCG_ERR_INVALID;
+  if (nx * ny > kNoallocMaxN) return PRCG_ERR_INVALID;
   const int64_t n = nx * ny * nz;
   if (n > kNoallocMaxN) return PRCG_ERR_INVALID;   // beyond the fixed scratch size
   if (precond != PRCG_PRECOND_NONE && precond != PRCG_PRECOND_JACOBI) return PRCG_ERR_INVALID;
   if (!(diag_shift >= 0.0) || !std::isfinite(diag_shift)) return PRCG_ERR_INVALID;
   if (!(tol >= 0.0) || maxit < 0 || !b || !x) return PRCG_ERR_INVALID;
-  if (!is_device_pointer(b) || !is_device_pointer(x)) return PRCG_ERR_INVALID;
-  if (residual_history && !is_device_pointer(residual_history)) return PRCG_ERR_INVALID;
+  if ((int64_t)maxit > kNoallocMaxItPerRow * n + kNoallocMaxItExtra) return PRCG_ERR_INVALID;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return PRCG_ERR_CUDA;
+  }
+  if (!is_device_pointer(b, dev) || !is_device_pointer(x, dev)) return PRCG_ERR_INVALID;
+  if (residual_history && !is_device_pointer(residual_history, dev)) return PRCG_ERR_INVALID;
   double* scratch = nullptr;
-  if (scratch_for_device(&scratch) != PRCG_OK) return PRCG_ERR_CUDA;
+  if (scratch_for_device(dev, &scratch) != PRCG_OK) return PRCG_ERR_CUDA;
   NoallocArgs a;
   a.dim = dim;
   a.nx = (int)nx;
