@@ -9,8 +9,8 @@ PR-CG to ||r_k|| / ||b|| <= 1e-10.  One step = one complete solve
 value = iterations / device time.  HS-CG, pipe-PR-CG, the matrix-free
 stencil and the 128^3 log-normal diffusion system are reported beside it.
 
---impl reference times the CPU oracle (plain numpy / scipy, one thread) on a
-bounded sample of the same workload.
+--impl reference times the CPU oracle (the multi-threaded C oracle on every
+host core) on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
@@ -46,7 +46,8 @@ def _peaks():
 
 
 # --------------------------------------------------------------------------- models
-def model_bytes(variant: str, op: str, precond: str, n: int, nnz: int, dim: int = 3) -> float:
+def model_bytes(variant: str, op: str, precond: str, n: int, nnz: int, dim: int = 3,
+                dvec=None) -> float:
     """Algorithmic DRAM bytes of one iteration, the fully fused minimum of the
     method (every vector read and written once per iteration, A read once).
 
@@ -66,7 +67,8 @@ def model_bytes(variant: str, op: str, precond: str, n: int, nnz: int, dim: int 
         A = (dim + 1) * V
     else:
         A = 0.0
-    dvec = precond == "jacobi" and op in ("csr", "varcoef")
+    if dvec is None:
+        dvec = precond == "jacobi" and op in ("csr", "varcoef")
     jac = precond == "jacobi"
     if variant == "hs":
         return 10 * V + A + (2 * V if dvec else 0.0)
@@ -77,7 +79,7 @@ def model_bytes(variant: str, op: str, precond: str, n: int, nnz: int, dim: int 
     raise KeyError(variant)
 
 
-def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int):
+def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int, dvec=None):
     """Per sweep of this library's schedule: (name, DRAM bytes the sweep must
     move, FP64 instructions it must execute), counted per row and x n.
 
@@ -92,7 +94,9 @@ def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int):
     V = 8.0 * n
     A = 12.0 * nnz + 4.0 * (n + 1) if op == "csr" else 0.0
     m = float(nnz) if op == "csr" else 1.0 * n
-    dv = 1.0 if (precond == "jacobi" and op == "csr") else 0.0   # read of vector d
+    if dvec is None:
+        dvec = precond == "jacobi" and op == "csr"
+    dv = 1.0 if dvec else 0.0   # read of vector d
     jac = precond == "jacobi"
     if variant == "hs":
         return [("k_hs_a", (6 + dv) * V, (5 if jac and dv else 3) * n),
@@ -130,7 +134,7 @@ def sweep_roofline(S, variant, op, precond, n, nnz, reps=20, sm_mhz=None):
     and place the slowest one on both rooflines (HBM bytes, FP64 issue)."""
     from paper_1905_01549_gb300 import binding
     ms = binding.prcg_time_sweeps(S.handle, binding.VARIANT_IDS[variant], reps)
-    models = sweep_models(variant, op, precond, n, nnz)
+    models = sweep_models(variant, op, precond, n, nnz, dvec=S.jacobi_form == "vector")
     peak_hbm, hbm_src = _peaks()
     peak_fp = fp64_peak(sm_mhz)
     per = []
@@ -393,7 +397,9 @@ def run_e2e(G, S, prob, variant, tol, maxit, args):
 
 
 def run_variants(G, prob, S_main, b_dev, args):
-    """HS vs PR vs pipe-PR on CSR and the matrix-free stencil (same system),
+    """HS vs PR vs pipe-PR on the four cells of the 256^3 configuration (CSR
+    and the matrix-free stencil, each with Jacobi and without a
+    preconditioner), every solve to the same final relative residual 1e-10,
     and the 128^3 log-normal diffusion system."""
     peak, _ = _peaks()
     out = {}
@@ -401,20 +407,29 @@ def run_variants(G, prob, S_main, b_dev, args):
     nnz = len(prob.csr[2])
     tol, maxit = 1e-10, 20000
     for op in ("csr", "stencil"):
-        S = S_main if op == "csr" else make_solver(G, prob, op, "jacobi")
-        for variant in ("hs", "pr", "pipe_pr"):
-            r = time_solves(S, b_dev, variant, tol, maxit, steps=2, warmup=1)
-            K = r["iters"][-1]
-            per = r["loop_ms"] / 1e3 / K
-            by = model_bytes(variant, op, "jacobi", n, nnz)
-            rf = sweep_roofline(S, variant, op, "jacobi", n, nnz if op == "csr" else 0)
-            out[f"{op}/jacobi/{variant}"] = {
-                "iters_per_s": sum(r["iters"]) / (sum(r["dev_ms"]) / 1e3), "iters": K,
-                "us_per_iter": per * 1e6, "algorithmic_gb_per_iter": by / 1e9,
-                "algorithmic_gbs": by / per / 1e9, "algorithmic_hbm_frac": by / per / 1e9 / peak,
-                "sweeps": rf["sweeps"], "status": r["status"]}
-        if op != "csr":
-            S.close()
+        for precond in ("jacobi", "none"):
+            main = op == "csr" and precond == args.precond and args.op == "csr"
+            S = S_main if main else make_solver(G, prob, op, precond)
+            cell = {}
+            for variant in ("hs", "pr", "pipe_pr"):
+                r = time_solves(S, b_dev, variant, tol, maxit, steps=2, warmup=1)
+                K = r["iters"][-1]
+                per = r["loop_ms"] / 1e3 / K
+                by = model_bytes(variant, op, precond, n, nnz)
+                rf = sweep_roofline(S, variant, op, precond, n, nnz if op == "csr" else 0)
+                chk = S.solve(b_dev, variant=variant, tol=tol, maxit=maxit, history=True,
+                              true_relres=True)
+                cell[variant] = {
+                    "iters_per_s": sum(r["iters"]) / (sum(r["dev_ms"]) / 1e3), "iters": K,
+                    "final_relres": float(chk.hist[-1]), "final_true_relres": chk.true_relres,
+                    "us_per_iter": per * 1e6, "algorithmic_gb_per_iter": by / 1e9,
+                    "algorithmic_gbs": by / per / 1e9, "algorithmic_hbm_frac": by / per / 1e9 / peak,
+                    "sweeps": rf["sweeps"], "status": r["status"], "jacobi_form": S.jacobi_form}
+                out[f"{op}/{precond}/{variant}"] = cell[variant]
+            out[f"{op}/{precond}/pr_over_hs"] = cell["pr"]["us_per_iter"] and \
+                cell["hs"]["us_per_iter"] / cell["pr"]["us_per_iter"]
+            if not main:
+                S.close()
     # variable-coefficient diffusion 128^3, sigma = 2, Jacobi
     import torch
     vc = build_problem("varcoef3d_128")
@@ -684,61 +699,84 @@ def run_dense(G, args):
     return out
 
 
-def oracle_sample(prob, variant, precond, iters):
-    """Seconds of `iters` oracle iterations (init time subtracted)."""
+def host_cores() -> int:
+    """Host cores this process may run on (its CPU affinity)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def c_oracle_loop(prob, variant, precond, iters, threads):
+    """Seconds of the main loop (initialize() excluded) of `iters` iterations
+    of the multi-threaded C oracle (oracle/cg_oracle.c), and its K."""
     import scipy.sparse as sp
     import oracle as O
-    rp, ci, v = prob.csr
-    A = sp.csr_matrix((v, ci, rp), shape=(prob.n, prob.n))
-    d = O.jacobi_inverse_diagonal(A) if precond == "jacobi" else None
-    t0 = time.perf_counter()
-    O.solve(variant, A, prob.b, d=d, tol=0.0, maxit=0)
-    t_init = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    O.solve(variant, A, prob.b, d=d, tol=0.0, maxit=iters)
-    t_run = time.perf_counter() - t0
-    return max(t_run - t_init, 1e-9), t_run
+    from oracle import c_oracle as C
+    d = None
+    if precond == "jacobi":
+        rp, ci, v = prob.csr
+        d = O.jacobi_inverse_diagonal(sp.csr_matrix((v, ci, rp), shape=(prob.n, prob.n)))
+    res = C.solve(variant, prob.csr, prob.b, d=d, tol=0.0, maxit=iters, threads=threads)
+    return res.loop_s, res.iters
+
+
+def cpu_sample_plan(prob, variant, precond, threads, budget_s=15.0, trials=3):
+    """Iterations per trial so that `trials` trials take about budget_s."""
+    t, k = c_oracle_loop(prob, variant, precond, 3, threads)
+    per = t / max(k, 1)
+    return int(min(200, max(5, budget_s / trials / max(per, 1e-6))))
 
 
 def run_cpu_baseline(prob, variant, precond, args):
-    iters = 6
-    t_loop, t_all = oracle_sample(prob, variant, precond, iters)
-    return {"value": iters / t_loop, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{iters} PR-CG iterations of the same 256^3 CSR Jacobi system "
-                      f"(numpy + scipy CSR matvec, one thread; initialisation timed "
-                      f"separately and subtracted; {t_all:.1f} s total)"}
+    """The C oracle on every host core: main loop only (initialize() timed
+    separately inside the oracle and left out, as the paper times only the
+    main loop), the minimum over 3 trials."""
+    cores = host_cores()
+    iters = cpu_sample_plan(prob, variant, precond, cores)
+    best = None
+    for _ in range(3):
+        t, k = c_oracle_loop(prob, variant, precond, iters, cores)
+        best = t if best is None else min(best, t)
+    return {"value": iters / best, "unit": "iters/s", "cores": cores, "kind": "oracle",
+            "sample": f"{iters} {variant.upper()}-CG iterations of the same {args.workload} "
+                      f"{args.op} {precond} system, C oracle (OpenMP, {cores} threads = the "
+                      f"process's CPU affinity, plain FP64 loops, CSR matvec); main loop only, "
+                      f"minimum of 3 trials ({best:.2f} s)"}
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step is a bounded sample (3
-    iterations) of the same workload on the host cores."""
+    """The oracle as the reference arm: the multi-threaded C oracle on every
+    host core, each step a bounded sample (the main loop of a fixed number of
+    iterations; initialize() is excluded and timed apart) of the same
+    workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import scipy.sparse as sp
-    import oracle as O
     prob = build_problem(args.workload)
-    rp, ci, v = prob.csr
-    A = sp.csr_matrix((v, ci, rp), shape=(prob.n, prob.n))
-    d = O.jacobi_inverse_diagonal(A)
-    per = 3
+    variant, precond = args.variant, args.precond
+    cores = host_cores()
+    per = cpu_sample_plan(prob, variant, precond, cores, budget_s=8.0, trials=1)
     for _ in range(args.warmup):
-        O.pr_cg(A, prob.b, d=d, tol=0.0, maxit=1)
-    t0 = time.perf_counter()
+        c_oracle_loop(prob, variant, precond, 1, cores)
+    tot, its = 0.0, 0
     for _ in range(args.steps):
-        O.pr_cg(A, prob.b, d=d, tol=0.0, maxit=per)
-    wall = time.perf_counter() - t0
-    value = per * args.steps / wall
+        t, k = c_oracle_loop(prob, variant, precond, per, cores)
+        tot += t
+        its += k
+    value = its / tot
     line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": tot * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": f"{args.workload}_csr_jacobi_pr", "n": prob.n, "nnz": len(v),
-                       "operator": "csr",
-                       "precond": "jacobi", "variant": "pr", "tol": 1e-10},
-            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step: oracle PR-CG initialisation + {per} iterations "
-                                       "(numpy + scipy, one thread)"},
+            "config": {"workload": f"{args.workload}_{args.op}_{precond}_{variant}", "n": prob.n,
+                       "nnz": len(prob.csr[2]), "operator": "csr", "precond": precond,
+                       "variant": variant, "tol": 1e-10},
+            "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step: the main loop of {per} {variant.upper()}-CG "
+                                       f"iterations of the C oracle (OpenMP, {cores} threads; "
+                                       "initialize() excluded); the CSR operator stands in for "
+                                       "the stencil"},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)

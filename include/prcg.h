@@ -96,6 +96,12 @@ enum prcg_status {
  * The arrays are copied into context-owned device memory (the caller may
  * free them afterwards).  Symmetry and definiteness are not checked up
  * front: a non-SPD A shows up as PRCG_BREAKDOWN during prcg_solve.
+ * With Jacobi, a diagonal whose entries are all bitwise equal is applied as
+ * one scalar d = 1 / a_11 (prcg_jacobi_form reports 1): each product d_i v_i
+ * is unchanged, the sweeps stop reading a d vector, and where a recurrence
+ * subtracts alpha M^{-1} v the scalar is folded into alpha (the same value
+ * up to rounding).  The environment variable PRCG_NO_SCALAR_D=1 keeps the
+ * vector form.
  * Returns PRCG_ERR_INVALID for inconsistent sizes or indices out of range.
  */
 int prcg_create_csr(prcg_ctx** out, int64_t n, int64_t nnz,
@@ -262,6 +268,13 @@ int prcg_time_sweeps(prcg_ctx* ctx, int variant, int reps, float* ms_per_sweep, 
 int prcg_last_launches(const prcg_ctx* ctx, int64_t* kernels);
 
 /* prcg_destroy -- free the context and everything it owns; NULL is a no-op. */
+/*
+ * prcg_jacobi_form -- how the context applies its preconditioner:
+ * 0 none, 1 a scalar d (constant stencils, or a CSR / dense diagonal whose
+ * entries are all equal), 2 a vector d.  Negative on a NULL context.
+ */
+int prcg_jacobi_form(const prcg_ctx* ctx);
+
 int prcg_destroy(prcg_ctx* ctx);
 
 /*
@@ -425,16 +438,24 @@ int prcg_batched_destroy(prcg_batch* bt);
  * loaded and kept by every GPU that loads it until the process exits:
  * n = nx*ny*nz must be <= 65536 (the array holds 8 vectors of 65536 doubles,
  * 4 MiB).  Larger n returns PRCG_ERR_INVALID.
- *   b, x              device pointers the caller owns (x: in x_0, out x_K)
- *   residual_history  NULL or device double[maxit + 1]
+ *   b, x              device pointers the caller owns (x: in x_0, out x_K),
+ *                     in memory of the current device (or managed memory);
+ *                     another GPU's memory returns PRCG_ERR_INVALID
+ *   tol, maxit        as prcg_solve; the solve is one kernel that cannot be
+ *                     interrupted, so maxit must be <= 4 n + 1000 (larger
+ *                     returns PRCG_ERR_INVALID): a tolerance the system cannot
+ *                     reach then ends with PRCG_NOT_CONVERGED in bounded time
+ *   residual_history  NULL or device double[maxit + 1] (current device)
  *   iters_out         NULL or receives K
  *   cuda_stream       stream to run on (NULL: legacy default stream)
+ * b == 0 gives x = 0 with K = 0, as prcg_solve does.
  * Returns PRCG_OK / PRCG_NOT_CONVERGED / PRCG_BREAKDOWN or a negative error.
  * Blocks until the result is known.  The first call on each device looks up
  * the array's device address (cudaGetSymbolAddress): make that first call
- * before any stream capture.  All calls share the one array, so calls that
- * overlap on the GPU (other streams or host threads) race with each other
- * and must be serialised by the caller.
+ * before any stream capture.  That set-up is safe when several host threads
+ * make their first call at once.  All calls share the one array, so calls
+ * that overlap on the GPU (other streams or host threads) race with each
+ * other and must be serialised by the caller.
  */
 int prcg_pr_solve_stencil_noalloc(int dim, int64_t nx, int64_t ny, int64_t nz,
                                   double diag_shift, int precond, const double* b, double* x,

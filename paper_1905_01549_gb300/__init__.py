@@ -81,6 +81,11 @@ class Solver:
         h = binding.prcg_create_dense(n, A, PRECONDS[precond], stream)
         return cls(h, n)
 
+    @property
+    def jacobi_form(self) -> str:
+        """How the preconditioner is applied: "none", "scalar" or "vector"."""
+        return ("none", "scalar", "vector")[binding.prcg_jacobi_form(self.handle)]
+
     def solve(self, b, x0=None, variant: str = "pr", tol: float = 1e-10,
               maxit: Optional[int] = None, history: bool = False,
               true_relres: bool = False, trace: bool = False) -> SolveResult:

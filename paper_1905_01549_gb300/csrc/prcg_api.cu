@@ -22,11 +22,14 @@
 
 namespace prcg {
 LaunchFn launcher_csr(int op_kind, int pc_kind);
+LaunchFn launcher_csr_scalar(int op_kind, int pc_kind);
 LaunchFn launcher_st(int op_kind, int pc_kind);
 LaunchFn launcher_vc(int op_kind, int pc_kind);
 LaunchFn launcher_dense(int op_kind, int pc_kind);
 
 LaunchFn launcher_for(int op_kind, int pc_kind) {
+  if ((op_kind == OP_CSR || op_kind == OP_SELL) && pc_kind == PC_SCALAR)
+    return launcher_csr_scalar(op_kind, pc_kind);
   if (op_kind == OP_CSR || op_kind == OP_SELL) return launcher_csr(op_kind, pc_kind);
   if (op_kind == OP_ST2 || op_kind == OP_ST3) return launcher_st(op_kind, pc_kind);
   if (op_kind == OP_DENSE) return launcher_dense(op_kind, pc_kind);
@@ -62,6 +65,17 @@ __global__ void k_csr_jacobi(const int* rp, const int* ci, const double* va, int
       d[i] = 1.0 / a;
     }
   }
+}
+
+// Flags (bit 8) a Jacobi diagonal that is not one constant: d_i != d_0
+// bitwise for some i.
+__global__ void k_const_diag(const double* d, int n, int* flag) {
+  const unsigned long long d0 = __double_as_longlong(d[0]);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    if ((unsigned long long)__double_as_longlong(d[i]) != d0) {
+      atomicOr(flag, 8);
+      return;
+    }
 }
 
 // Guard bands: 256-byte blocks after every vector and partial-sum buffer,
@@ -738,6 +752,27 @@ int prcg_create_csr(prcg_ctx** out, int64_t n, int64_t nnz, const int32_t* row_p
     k_csr_jacobi<<<c->plan.sms * 4, 256, 0, c->cs>>>(rp, ci, va, (int)n,
                                                     const_cast<double*>(c->plan.pc.d), c->dbad);
     if ((rc = check_bad(c, "Jacobi needs a positive diagonal")) != PRCG_OK) return fail(rc);
+    // A diagonal that is one constant (every d_i bitwise equal) is applied as
+    // a scalar: the product d_i v_i is the same, the sweeps stop reading d,
+    // and d folds into alpha where a recurrence subtracts alpha M^{-1} v.
+    const char* nsc = getenv("PRCG_NO_SCALAR_D");
+    if (!(nsc && nsc[0] == '1')) {
+      int flag = 0;
+      double d0 = 0.0;
+      if (cudaMemsetAsync(c->dbad, 0, sizeof(int), c->cs) != cudaSuccess)
+        return fail(cuda_err(c, cudaGetLastError(), "memset"));
+      k_const_diag<<<c->plan.sms * 4, 256, 0, c->cs>>>(c->plan.pc.d, (int)n, c->dbad);
+      cudaMemcpyAsync(&flag, c->dbad, sizeof(int), cudaMemcpyDeviceToHost, c->cs);
+      cudaMemcpyAsync(&d0, c->plan.pc.d, sizeof(double), cudaMemcpyDeviceToHost, c->cs);
+      if (cudaStreamSynchronize(c->cs) != cudaSuccess)
+        return fail(cuda_err(c, cudaGetLastError(), "constant-diagonal check"));
+      if (cudaMemsetAsync(c->dbad, 0, sizeof(int), c->cs) != cudaSuccess)
+        return fail(cuda_err(c, cudaGetLastError(), "memset"));
+      if (flag == 0) {
+        c->plan.pc.kind = PC_SCALAR;
+        c->plan.pc.dscalar = d0;
+      }
+    }
   }
   const char* ns = getenv("PRCG_NO_SELL");
   if (!(ns && ns[0] == '1')) {
@@ -1288,6 +1323,11 @@ int prcg_last_launches(const prcg_ctx* c, int64_t* kernels) {
   if (!c || !kernels) return PRCG_ERR_INVALID;
   *kernels = c->last_launches;
   return PRCG_OK;
+}
+
+int prcg_jacobi_form(const prcg_ctx* c) {
+  if (!c) return PRCG_ERR_INVALID;
+  return c->plan.pc.kind == PC_SCALAR ? 1 : c->plan.pc.kind == PC_VEC ? 2 : 0;
 }
 
 int prcg_destroy(prcg_ctx* c) {
