@@ -12,13 +12,11 @@ import pytest
 
 import oracle as O
 import problems as P
-from gpu_common import CASES, case, csr_matrix, make_solver, oracle_spread, rel
+from gpu_common import CASES, ITER_TOL, OracleBand, case, csr_matrix, make_solver, rel
 
 pytestmark = pytest.mark.gpu
 
-ITER_TOL = 1e-10
 HIST_TOL = 1e-9
-SPREAD_FACTOR = 100.0
 
 # GPU variant name -> (oracle variant, oracle option that switches the recompute off)
 ABLATIONS = {"pr_norecompute": ("pr", {"recompute_nu": False}),
@@ -47,23 +45,25 @@ def test_ablation_first_20_iterations(G, name, op, precond):
     b = torch.from_numpy(prob.b).cuda()
     with make_solver(G, prob, op, precond) as S:
         for gv, (ov, kw) in ABLATIONS.items():
-            for k in (1, 2, 7, 20):
+            band = OracleBand(ov, A, prob.b, d, 20, **kw)
+            for k in (1, 2, 7, 10, 15, 20):
                 res = S.solve(b, variant=gv, tol=0.0, maxit=k, history=True)
-                ref, sx, sh = oracle_spread(ov, A, prob.b, d, k, **kw)
-                assert res.status == ref.status == O.NOT_CONVERGED, (gv, res.status)
+                assert res.status == band.ref.status == O.NOT_CONVERGED, (gv, res.status)
                 assert res.iters == k
-                tol_x = max(ITER_TOL, SPREAD_FACTOR * sx)
-                tol_h = max(HIST_TOL, SPREAD_FACTOR * sh)
-                assert rel(res.x.cpu().numpy(), ref.x) <= tol_x, (gv, k, tol_x)
-                h = np.asarray(ref.hist)
-                assert np.all(np.abs(res.hist - h) <= tol_h * h), (gv, k, tol_h)
-                # without the recompute the iterates are themselves more
-                # sensitive to rounding (carried nu' drifts: on poisson3d_ragged
-                # a change of summation order alone moves x_20 by ~1e-10), so
-                # the spread sets the bar here; it stays small where the
-                # system is well conditioned
+                ok_h, worst_h = band.hist_ok(k, res.hist, HIST_TOL)
+                assert ok_h, (gv, k, worst_h)
+                # without the recompute the iterates are more sensitive to
+                # rounding than the variants' (a carried nu' drifts), so the
+                # oracle's spread sets the bar more often; on well-conditioned
+                # systems every checkpoint is still compared element by element
                 if name in ("poisson2d_64", "poisson3d_ragged", "shifted2d") or precond == "jacobi":
-                    assert tol_x <= 1e-7, (gv, k, tol_x)
+                    assert band.determined(k), (gv, k, band.spread_x(k))
+                if band.determined(k):
+                    xg = res.x.cpu().numpy()
+                    assert band.dist_x(k, xg) <= band.bar_x(k), (gv, k, band.dist_x(k, xg),
+                                                                 band.bar_x(k))
+                else:
+                    assert k >= 15, (gv, k, band.spread_x(k))
 
 
 def test_ablations_differ_from_the_recompute_variants(G):

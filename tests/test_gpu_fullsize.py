@@ -1,10 +1,21 @@
 """Full-size checks at the benchmark sizes (256^3 7-point Poisson, 128^3
 log-normal diffusion), in the launch configuration the benchmark times.
 
-The oracle cannot iterate to convergence at n = 16.8M in test time, so the
-first iterations are compared element by element and the converged solve is
-checked through properties that hold at any size (status, final true
-residual, monotone history envelope)."""
+* The first 20 iterations at 256^3 -- CSR and the matrix-free stencil,
+  Jacobi and no preconditioner, PR-CG (Algorithm 2), HS-CG (Algorithm 1) and
+  pipe-PR-CG (Algorithm 3) -- element by element against the oracle: x_20
+  within 1e-10 relative and ||r_k|| / ||b|| for every k <= 20 within 1e-9.
+  Poisson's iterates are insensitive to rounding this early (the oracle's
+  spread over other rounding orders stays near 1e-15 on the smaller Poisson
+  cases), so the plain 1e-10 bar applies.
+* The iteration count to ||r_K|| / ||b|| <= 1e-10 within 5 % of the
+  oracle's, read from tests/golden/iteration_counts.txt (written by
+  tests/golden/make_iteration_counts.py, which calls only the oracle).
+* The converged solve through properties that hold at any size (status,
+  final true residual, decreasing residual envelope).
+"""
+import os
+
 import numpy as np
 import pytest
 
@@ -13,6 +24,10 @@ import problems as P
 from gpu_common import csr_matrix, rel
 
 pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                      "iteration_counts.txt")
+K20 = 20
 
 
 @pytest.fixture(scope="module")
@@ -31,52 +46,117 @@ def p256():
     return P.poisson3d(256)
 
 
-@pytest.mark.parametrize("variant", ["pr", "hs", "pipe_pr"])
-@pytest.mark.parametrize("op", ["csr", "stencil"])
-def test_256_first_iterations(G, p256, variant, op):
-    import torch
+@pytest.fixture(scope="module")
+def oracle20(p256):
+    """The oracle's first 20 iterations at 256^3, computed once per
+    (variant, preconditioner) and shared by the CSR and stencil cases."""
     A = csr_matrix(p256)
-    d = O.jacobi_inverse_diagonal(A)
-    b = torch.from_numpy(p256.b).cuda()
-    ref = O.solve(variant, A, p256.b, d=d, tol=0.0, maxit=3)
+    cache = {}
+
+    def get(variant, precond):
+        key = (variant, precond)
+        if key not in cache:
+            d = O.jacobi_inverse_diagonal(A) if precond == "jacobi" else None
+            cache[key] = O.solve(variant, A, p256.b, d=d, tol=0.0, maxit=K20)
+        return cache[key]
+    return get
+
+
+def _solver(G, prob, op, precond):
     if op == "csr":
-        rp, ci, v = p256.csr
-        S = G.Solver.from_csr(rp, ci, v, precond="jacobi")
-    else:
-        S = G.Solver.from_stencil(p256.dims, precond="jacobi")
-    with S:
-        res = S.solve(b, variant=variant, tol=0.0, maxit=3, history=True)
-        assert res.iters == 3
-        assert rel(res.x.cpu().numpy(), ref.x) <= 1e-10
-        assert np.allclose(res.hist, ref.hist, rtol=1e-9, atol=0)
+        rp, ci, v = prob.csr
+        return G.Solver.from_csr(rp, ci, v, precond=precond)
+    return G.Solver.from_stencil(prob.dims, face_coeff=prob.face_array(), precond=precond)
 
 
-@pytest.mark.parametrize("variant", ["pr", "hs", "pipe_pr"])
-def test_256_converges_to_1e10(G, p256, variant):
+def golden_counts():
+    """{(system, variant, precond): K} from the oracle-written fixture."""
+    out = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if line:
+                out[(line[0], line[1], line[2])] = int(line[3])
+    return out
+
+
+@pytest.mark.parametrize("precond", ["jacobi", "none"])
+@pytest.mark.parametrize("op", ["csr", "stencil"])
+def test_256_first_20_iterations(G, p256, oracle20, op, precond):
     import torch
     b = torch.from_numpy(p256.b).cuda()
-    rp, ci, v = p256.csr
-    with G.Solver.from_csr(rp, ci, v, precond="jacobi") as S:
-        res = S.solve(b, variant=variant, tol=1e-10, maxit=20000, history=True, true_relres=True)
-    assert res.status == G.PRCG_OK and res.hist[-1] <= 1e-10
-    assert res.true_relres <= 1e-9
-    # the residual envelope decreases: each 100-iteration window ends lower
-    h = res.hist
-    lows = [h[i:i + 100].min() for i in range(0, len(h) - 100, 100)]
-    assert all(b_ < a_ for a_, b_ in zip(lows, lows[1:]))
+    with _solver(G, p256, op, precond) as S:
+        for variant in ("pr", "hs", "pipe_pr"):
+            ref = oracle20(variant, precond)
+            res = S.solve(b, variant=variant, tol=0.0, maxit=K20, history=True)
+            assert res.status == ref.status == O.NOT_CONVERGED and res.iters == K20
+            assert rel(res.x.cpu().numpy(), ref.x) <= 1e-10, (variant, op, precond)
+            h = np.asarray(ref.hist)
+            assert np.all(np.abs(res.hist - h) <= 1e-9 * h), (variant, op, precond)
 
 
-def test_varcoef128_first_iterations(G):
+@pytest.mark.parametrize("precond", ["jacobi", "none"])
+@pytest.mark.parametrize("op", ["csr", "stencil"])
+def test_256_iteration_count_matches_oracle(G, p256, op, precond):
+    """Iterations to 1e-10 within 5 % of the oracle's, and the converged
+    solve's properties."""
     import torch
-    prob = P.varcoef3d(128)
+    golden = golden_counts()
+    b = torch.from_numpy(p256.b).cuda()
+    with _solver(G, p256, op, precond) as S:
+        for variant in ("pr", "hs", "pipe_pr"):
+            k_ref = golden[("poisson3d_256", variant, precond)]
+            res = S.solve(b, variant=variant, tol=1e-10, maxit=20000, history=True,
+                          true_relres=True)
+            assert res.status == G.PRCG_OK and res.hist[-1] <= 1e-10
+            assert abs(res.iters - k_ref) <= 0.05 * k_ref, (variant, op, precond, res.iters, k_ref)
+            assert res.true_relres <= 1e-9
+            # the residual envelope decreases: each 100-iteration window ends lower
+            h = res.hist
+            lows = [h[i:i + 100].min() for i in range(0, len(h) - 100, 100)]
+            assert all(b_ < a_ for a_, b_ in zip(lows, lows[1:]))
+
+
+@pytest.fixture(scope="module")
+def vc128():
+    return P.varcoef3d(128)
+
+
+def test_varcoef128_first_iterations_and_count(G, vc128):
+    import torch
+    prob = vc128
     A = csr_matrix(prob)
     d = O.jacobi_inverse_diagonal(A)
     b = torch.from_numpy(prob.b).cuda()
-    rp, ci, v = prob.csr
-    for S in (G.Solver.from_csr(rp, ci, v, precond="jacobi"),
-              G.Solver.from_stencil(prob.dims, face_coeff=prob.face_array(), precond="jacobi")):
-        with S:
+    golden = golden_counts()
+    refs = {v: O.solve(v, A, prob.b, d=d, tol=0.0, maxit=K20) for v in ("pr", "hs", "pipe_pr")}
+    for op in ("csr", "stencil"):
+        with _solver(G, prob, op, "jacobi") as S:
             for variant in ("pr", "hs", "pipe_pr"):
-                ref = O.solve(variant, A, prob.b, d=d, tol=0.0, maxit=4)
-                res = S.solve(b, variant=variant, tol=0.0, maxit=4)
-                assert rel(res.x.cpu().numpy(), ref.x) <= 1e-10
+                ref = refs[variant]
+                res = S.solve(b, variant=variant, tol=0.0, maxit=K20, history=True)
+                assert rel(res.x.cpu().numpy(), ref.x) <= 1e-10, (op, variant)
+                h = np.asarray(ref.hist)
+                assert np.all(np.abs(res.hist - h) <= 1e-9 * h), (op, variant)
+                k_ref = golden[("varcoef3d_128", variant, "jacobi")]
+                res = S.solve(b, variant=variant, tol=1e-10, maxit=20000, true_relres=True)
+                assert res.status == G.PRCG_OK
+                assert abs(res.iters - k_ref) <= 0.05 * k_ref, (op, variant, res.iters, k_ref)
+                assert res.true_relres <= 1e-9
+
+
+def test_poisson2d_64_iteration_count(G):
+    """The synchronisation-bound configuration (2D 64^2, CSR, no
+    preconditioner): iterations to 1e-10 within 5 % of the oracle's."""
+    import torch
+    prob = P.poisson2d_64()
+    golden = golden_counts()
+    b = torch.from_numpy(prob.b).cuda()
+    for op in ("csr", "stencil"):
+        with _solver(G, prob, op, "none") as S:
+            for variant in ("pr", "hs", "pipe_pr"):
+                for pc in ("none",):
+                    k_ref = golden[("poisson2d_64", variant, pc)]
+                    res = S.solve(b, variant=variant, tol=1e-10, maxit=2 * prob.n)
+                    assert res.status == G.PRCG_OK
+                    assert abs(res.iters - k_ref) <= 0.05 * k_ref, (op, variant, res.iters, k_ref)

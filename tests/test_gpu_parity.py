@@ -3,18 +3,23 @@
 Bar (from the method's statement of the target): FP64 iterates within 1e-10
 relative of the oracle over the first 20 iterations, the iteration count to
 the tolerance within 5 %, and the final true residual at the tolerance.
+Where a system makes the iterates themselves sensitive to rounding order,
+the bar is 8 x the oracle's own spread over three other roundings,
+never above 1e-6 (gpu_common.OracleBand); past that point properties are
+checked instead.
 """
 import numpy as np
 import pytest
+import scipy.sparse.linalg as spla
 
 import oracle as O
-from gpu_common import CASES, GPU_VARIANTS, case, csr_matrix, make_solver, oracle_spread, rel
+from gpu_common import (CASES, GPU_VARIANTS, ITER_TOL, OracleBand, case,
+                        csr_matrix, make_solver, rel)
 
 pytestmark = pytest.mark.gpu
 
-ITER_TOL = 1e-10     # relative, first 20 iterations
 HIST_TOL = 1e-9      # per entry of ||r_k|| / ||b||
-SPREAD_FACTOR = 100.0
+KS = (1, 2, 7, 10, 15, 20)
 
 
 @pytest.fixture(scope="module")
@@ -49,6 +54,10 @@ def _oracle_d(A, precond):
     return O.jacobi_inverse_diagonal(A) if precond == "jacobi" else None
 
 
+def _well_conditioned(name, precond):
+    return name in ("poisson2d_64", "poisson3d_ragged", "shifted2d") or precond == "jacobi"
+
+
 @pytest.mark.parametrize("name", CASES)
 @pytest.mark.parametrize("op", ["csr", "stencil"])
 @pytest.mark.parametrize("precond", ["none", "jacobi"])
@@ -58,20 +67,39 @@ def test_first_20_iterations(G, torch_mod, name, op, precond):
     A = csr_matrix(prob)
     d = _oracle_d(A, precond)
     b = torch.from_numpy(prob.b).cuda()
+    xstar = None
     with make_solver(G, prob, op, precond) as S:
         for variant in GPU_VARIANTS:
-            for k in (1, 2, 7, 20):
+            band = OracleBand(variant, A, prob.b, d, KS[-1])
+            prev_ea = None
+            for k in KS:
                 res = S.solve(b, variant=variant, tol=0.0, maxit=k, history=True)
-                ref, sx, sh = oracle_spread(variant, A, prob.b, d, k)
-                assert res.status == ref.status == O.NOT_CONVERGED
-                assert res.iters == k
-                tol_x = max(ITER_TOL, SPREAD_FACTOR * sx)
-                tol_h = max(HIST_TOL, SPREAD_FACTOR * sh)
-                assert rel(res.x.cpu().numpy(), ref.x) <= tol_x, (variant, k, tol_x)
-                h = np.asarray(ref.hist)
-                assert np.all(np.abs(res.hist - h) <= tol_h * h), (variant, k, tol_h)
-                if name in ("poisson2d_64", "poisson3d_ragged", "shifted2d") or precond == "jacobi":
-                    assert tol_x == ITER_TOL  # well-conditioned: the plain 1e-10 bar
+                assert res.status == O.NOT_CONVERGED and res.iters == k
+                xg = res.x.cpu().numpy()
+                ok_h, worst_h = band.hist_ok(k, res.hist, HIST_TOL)
+                assert ok_h, (variant, k, worst_h)
+                if _well_conditioned(name, precond):
+                    assert band.bar_x(k) == ITER_TOL, (variant, k, band.spread_x(k))
+                if not _well_conditioned(name, precond):
+                    # CG minimises the A-norm error: it decreases from one
+                    # checkpoint to the next on the GPU's own iterates
+                    if xstar is None:
+                        xstar = spla.spsolve(A.tocsc(), prob.b)
+                    ea = O.a_norm_error(A, xstar, xg)
+                    if prev_ea is not None:
+                        assert ea <= prev_ea, (variant, k)
+                    prev_ea = ea
+                if band.determined(k):
+                    assert band.dist_x(k, xg) <= band.bar_x(k), (variant, k, band.dist_x(k, xg),
+                                                                 band.bar_x(k))
+                    continue
+                # x_k is not determined to DETERMINED by FP64 arithmetic (an
+                # unpreconditioned sigma = 2 diffusion case near k = 20): its
+                # A-norm error, which CG minimises, agrees with the oracle
+                # runs' to 1 % (they spread by up to ~5e-3 among themselves)
+                assert k >= 15, (variant, k, band.spread_x(k))
+                eas = [O.a_norm_error(A, xstar, r.iterates[k][0]) for r in band.runs]
+                assert min(abs(ea - e) / e for e in eas) <= 1e-2, (variant, k, ea, eas)
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -279,10 +307,11 @@ def test_point_source_mixes_fallback_and_fixed_point_rows(G, torch_mod, name, pa
             for k in (1, 3, 8, 20):
                 res = S.solve(torch.from_numpy(b).cuda(), variant=variant, tol=0.0, maxit=k,
                               history=True)
-                ref, sx, sh = oracle_spread(variant, A, b, None, k)
-                assert res.iters == ref.iters == k, (variant, k)
-                tol_x = max(ITER_TOL, SPREAD_FACTOR * sx)
-                assert rel(res.x.cpu().numpy(), ref.x) <= tol_x, (variant, k, tol_x)
+                band = OracleBand(variant, A, b, None, k)
+                assert res.iters == band.ref.iters == k, (variant, k)
+                assert band.determined(k), (variant, k, band.spread_x(k))
+                xg = res.x.cpu().numpy()
+                assert band.dist_x(k, xg) <= band.bar_x(k), (variant, k, band.bar_x(k))
 
 
 @pytest.mark.parametrize("path", ["persistent", "graph"])
@@ -316,3 +345,37 @@ def test_graph_path_reruns_are_bitwise_identical(G, torch_mod, monkeypatch):
             r2 = S.solve(b, variant=variant, tol=1e-10, maxit=5000, history=True)
             assert r1.iters == r2.iters
             assert torch.equal(r1.x, r2.x) and np.array_equal(r1.hist, r2.hist)
+
+
+@pytest.mark.parametrize("path", ["persistent", "graph"])
+def test_constant_csr_diagonal_runs_as_scalar(G, torch_mod, path, monkeypatch):
+    """A CSR matrix whose diagonal is one constant (Poisson) applies Jacobi as
+    a scalar; forced back to the d vector (PRCG_NO_SCALAR_D=1) the iterates
+    are the same to the parity bar, and both match the oracle.  A varying
+    diagonal keeps the vector."""
+    torch = torch_mod
+    if path == "graph":
+        monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    prob = case("poisson3d_ragged")
+    A = csr_matrix(prob)
+    d = O.jacobi_inverse_diagonal(A)
+    b = torch.from_numpy(prob.b).cuda()
+    forms = {}
+    xs = {}
+    for env in ("0", "1"):
+        monkeypatch.setenv("PRCG_NO_SCALAR_D", env)
+        with make_solver(G, prob, "csr", "jacobi") as S:
+            forms[env] = S.jacobi_form
+            for variant in GPU_VARIANTS:
+                res = S.solve(b, variant=variant, tol=0.0, maxit=20)
+                xs[(env, variant)] = res.x.cpu().numpy()
+    assert forms == {"0": "scalar", "1": "vector"}
+    for variant in GPU_VARIANTS:
+        ref = O.solve(variant, A, prob.b, d=d, tol=0.0, maxit=20)
+        for env in ("0", "1"):
+            assert rel(xs[(env, variant)], ref.x) <= ITER_TOL, (variant, env)
+    monkeypatch.setenv("PRCG_NO_SCALAR_D", "0")
+    with make_solver(G, case("varcoef3d_ragged"), "csr", "jacobi") as S:
+        assert S.jacobi_form == "vector"
+    with make_solver(G, prob, "csr", "none") as S:
+        assert S.jacobi_form == "none"
