@@ -267,6 +267,23 @@ int prcg_time_sweeps(prcg_ctx* ctx, int variant, int reps, float* ms_per_sweep, 
  */
 int prcg_last_launches(const prcg_ctx* ctx, int64_t* kernels);
 
+/*
+ * prcg_last_fixed_sweeps -- how many product sweeps (s = A p) of the last
+ * prcg_solve read the block fixed-point copy of p.  On a constant-
+ * coefficient stencil the graph path of HS-CG and PR-CG / M-CG stores, in
+ * the sweep that forms p, P_i = round(p_i 2^S) as a 64-bit integer with one
+ * scale S per vector, chosen from upper bounds of the vectors p is formed
+ * from so that every |P_i| < 2^58; the product sweep then adds the 2*dim
+ * neighbour values with integer adds and rounds the sum once to FP64.  The
+ * error of the neighbour sum is at most 2^-(S+1) per term plus that one
+ * rounding: a normwise bound, below 2^-58 max |p| per term, instead of the
+ * per-row bound of the fixed-point sum of the other sweeps.  A value
+ * outside its window (never expected) makes that sweep use the per-row
+ * sums; PRCG_NO_FIXED_P=1 disables the copy.  0 for the persistent path and
+ * for other operators and variants.
+ */
+int prcg_last_fixed_sweeps(const prcg_ctx* ctx, int64_t* sweeps);
+
 /* prcg_destroy -- free the context and everything it owns; NULL is a no-op. */
 /*
  * prcg_jacobi_form -- how the context applies its preconditioner:

@@ -289,6 +289,7 @@ struct prcg_ctx {
   float t_init = 0.f, t_loop = 0.f;
   int last_iters = 0;
   int64_t last_launches = 0;
+  int64_t last_pf_sweeps = 0;   // product sweeps of the last solve that read the fixed-point p
   int64_t host_loop_launches = 0;
   float* pool32 = nullptr;       // FP32 vectors of the mixed-precision inner solve
   float* sval32 = nullptr;       // FP32 copy of the SELL values
@@ -328,6 +329,14 @@ int cuda_err(prcg_ctx* c, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_err(c, e_, #call); \
   } while (0)
 
+// The constant-stencil product sweeps of HS-CG and PR-CG read a block
+// fixed-point copy of p unless PRCG_NO_FIXED_P=1 (then the per-row
+// fixed-point neighbour sums are used).
+int fixed_p_allowed() {
+  const char* e = getenv("PRCG_NO_FIXED_P");
+  return (e && e[0] == '1') ? 0 : 1;
+}
+
 // Register and fill a guard band of `words` 8-byte words at p.
 int add_guard(prcg_ctx* c, void* p, size_t words) {
   c->guards.emplace_back(p, words);
@@ -349,10 +358,11 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   CK(cudaEventCreate(&c->ev_start));
   CK(cudaEventCreate(&c->ev_init));
   CK(cudaEventCreate(&c->ev_loop));
-  // 18 n-vectors: x, b, t, d and two buffers each of r, r~, p, s, s~, w, u;
-  // each starts on a 256-byte boundary and is followed by a guard band that
-  // covers its rounding up to 32 entries and 32 more words
-  const size_t nv = 18;
+  // 19 n-vectors: x, b, t, d, two buffers each of r, r~, p, s, s~, w, u, and
+  // the block fixed-point copy of p (64-bit integers); each starts on a
+  // 256-byte boundary and is followed by a guard band that covers its
+  // rounding up to 32 entries and 32 more words
+  const size_t nv = 19;
   const size_t nr = ((size_t)n + 31) / 32 * 32, stride = nr + kGuardWords;
   CK(cudaMalloc(&c->pool, (kGuardWords + nv * stride) * sizeof(double)));
   int grc = add_guard(c, c->pool, kGuardWords);
@@ -369,6 +379,7 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   V.x = take();
   V.b = take();
   V.t = take();
+  V.pf = reinterpret_cast<long long*>(take());
   double* d = take();
   for (int k = 0; k < 2; ++k) {
     V.r[k] = take();
@@ -959,6 +970,7 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   h.maxbodies = maxit / chunk + 3;
   h.status = kRunning;
   h.carry_nu = variant == V_PR_NR ? 1 : 0;
+  h.pf_allow = fixed_p_allowed();
   CK(cudaMemcpyAsync(c->S, &h, sizeof h, cudaMemcpyHostToDevice, c->cs));
   CK(cudaEventRecord(c->ev_start, c->cs));
   bool persisted = false;
@@ -991,6 +1003,7 @@ int prcg_solve(prcg_ctx* c, int variant, const double* b, double* x, double tol,
   }
   CK(cudaMemcpyAsync(&h, c->S, sizeof h, cudaMemcpyDeviceToHost, c->cs));
   CK(cudaStreamSynchronize(c->cs));
+  c->last_pf_sweeps = h.pf_sweeps;
   const int K = h.k;
   {
     const int64_t per_iter = iter_launches(variant) + product_prepasses(c);
@@ -1079,6 +1092,7 @@ int prcg_time_sweeps(prcg_ctx* c, int variant, int reps, float* ms_per_sweep, in
   h.status = kRunning;
   h.profile = 1;
   h.maxbodies = 1 << 30;
+  h.pf_allow = fixed_p_allowed();
   double tsum[3] = {0, 0, 0};
   cudaError_t e = cudaMemsetAsync(c->plan.v.x, 0, (size_t)c->n * sizeof(double), c->cs);
   if (e == cudaSuccess) {
@@ -1316,6 +1330,12 @@ int prcg_last_timing(const prcg_ctx* c, float* init_ms, float* loop_ms, int* ite
   if (init_ms) *init_ms = c->t_init;
   if (loop_ms) *loop_ms = c->t_loop;
   if (iters) *iters = c->last_iters;
+  return PRCG_OK;
+}
+
+int prcg_last_fixed_sweeps(const prcg_ctx* c, int64_t* sweeps) {
+  if (!c || !sweeps) return PRCG_ERR_INVALID;
+  *sweeps = c->last_pf_sweeps;
   return PRCG_OK;
 }
 

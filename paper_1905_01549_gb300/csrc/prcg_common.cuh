@@ -50,6 +50,15 @@ struct DevState {
   double arg;            // mixed precision: 1 / ||t|| of the current refinement step
   double* trace;         // optional scalar trace, (maxit + 2) x kTraceFields, or NULL
   int carry_nu;          // 1: nu_k := nu'_k for k >= 1 (the PR-CG ablation of Fig. 1)
+  // Block fixed-point copy of p for the constant-stencil product sweeps of
+  // HS-CG and PR-CG (prcg_isum.cuh, to_fixed): the scale of the next copy
+  // is chosen from bounds of the magnitudes of the vectors that form p.
+  int pf_allow;          // set by the host: 0 keeps the per-row fixed-point sums
+  int pf_on;             // the sweep that forms p also stores its fixed-point copy
+  int pf_scale;          // S of that copy: P_i = round(p_i 2^S)
+  int pf_bad;            // a value of the copy did not fit its window (fall back)
+  unsigned amax_r, amax_p, amax_s;   // high words (sign cleared) of max |r~|, |p|, |s|
+  int pf_sweeps;         // product sweeps of this solve that read the fixed-point copy
 };
 
 // Scalar trace: slot k holds the scalars of iteration k in the oracle's
@@ -78,6 +87,7 @@ struct Vecs {
   double* w[2];
   double* u[2];
   double* t;             // scratch vector (true residual, GV's t_k)
+  long long* pf;         // block fixed-point copy of p (constant stencils)
 };
 
 // FP32 vectors of the mixed-precision inner solve (A d = r in FP32).
@@ -199,6 +209,23 @@ __device__ __forceinline__ void scalar_step_pr(DevState* S, bool meurant) {
   trace(S, S->k + 1, TR_ALPHA, alpha);
   trace(S, S->k + 1, TR_NU_PRED, nu_pred);
   trace(S, S->k + 1, TR_BETA, S->beta);
+}
+
+// CTA-wide maximum of v (thread-local values), added to *dst with one
+// global atomicMax by thread 0.  Every thread of the CTA must call it.
+__device__ __forceinline__ void cta_atomic_max(unsigned v, unsigned* dst) {
+  __shared__ unsigned smax;
+  if (threadIdx.x == 0) smax = 0u;
+  __syncthreads();
+  v = __reduce_max_sync(0xffffffffu, v);
+  if ((threadIdx.x & 31) == 0 && v) atomicMax(&smax, v);
+  __syncthreads();
+  if (threadIdx.x == 0 && smax) atomicMax(dst, smax);
+}
+
+// Magnitude key of a double for the max trackers: its high word, sign cleared.
+__device__ __forceinline__ unsigned mag_hi(double v) {
+  return (unsigned)__double2hiint(v) & 0x7FFFFFFFu;
 }
 
 // The reduction of iteration k of PR-CG / pipe-PR-CG (values already in S).

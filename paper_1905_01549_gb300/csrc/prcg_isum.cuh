@@ -152,6 +152,76 @@ __host__ __device__ __forceinline__ bool fixed_point_sum(const double (&v)[K], d
   return true;
 }
 
+// ---------------------------------------------------------------------------
+// Block fixed point with one scale per vector.
+//
+// The sweep that forms p also stores P_i = round(p_i 2^S) as a 64-bit
+// integer, with one scale S for the whole vector, chosen before the sweep
+// from an upper bound B >= max |p_i| so that B 2^S < 2^58 (to_fixed flags a
+// value that does not fit).  The product sweep then adds the 2*dim
+// neighbour values P_j with 64-bit integer adds and converts the sum once,
+// exactly rounded, to FP64 (fixed_to_double).  The sum of the P_j is exact;
+// the only errors are the roundings of the P_j (at most 2^-(S+1) each, i.e.
+// 2^-59 B per term) and the one final rounding -- a normwise bound (relative
+// to B, not to the row's own terms) far below the FP64 product's
+// eps ||A|| ||p||.
+
+// round(v 2^S) for |v| 2^S < 2^58 (half-way cases away from zero).  Zero,
+// subnormal v and values below half a unit give 0; a value too large for
+// the window, an infinity or a NaN sets bad.
+__host__ __device__ __forceinline__ long long to_fixed(double v, int S, bool& bad) {
+  const unsigned hi = isum_hi(v), lo = isum_lo(v);
+  const int e = (int)((hi >> 20) & 0x7FFu);
+  if (e == 0) return 0;
+  // the significand m (53 bits) shifted up by 5: v 2^S = (m << 5) 2^(e - 1080 + S)
+  const int t = 1080 - S - e;
+  if (e == 0x7FF || t < 0) {
+    bad = true;
+    return 0;
+  }
+  if (t > 63) return 0;
+  const uint64_t m = ((((uint64_t)((hi & 0xFFFFFu) | 0x100000u)) << 32) | lo) << 5;
+  // m / 2^t rounded half away from zero (t == 0: exact)
+  const uint64_t q = t == 0 ? m : ((m >> (t - 1)) + 1) >> 1;
+  return (hi >> 31) ? -(long long)q : (long long)q;
+}
+
+// acc 2^-S as the nearest double (ties to even); |acc| < 2^63, and the
+// scale keeps the result a normal number (|S| <= 900).
+__host__ __device__ __forceinline__ double fixed_to_double(long long acc, int S) {
+  if (acc == 0) return 0.0;
+  const long long sm = acc >> 63;
+  uint64_t a = (uint64_t)((acc ^ sm) - sm);
+  const int lz = isum_clz64(a);
+  a <<= lz;
+  uint64_t mant = a >> 11;   // 53 bits, the leading one at bit 52
+  const unsigned rem = (unsigned)a & 0x7FFu;
+  mant += (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+  // value = a 2^-(lz + S) with a's leading one at bit 63: biased exponent
+  // 1023 + 63 - lz - S; adding the significand (leading one included) to
+  // (exponent - 1) << 52 also carries a rounding overflow
+  const uint64_t bits = ((uint64_t)(1085 - lz - S) << 52) + mant;
+  return isum_from_bits(bits | ((uint64_t)sm << 63));
+}
+
+// Scale S of a vector whose entries are bounded by B: the largest S with
+// B 2^S < 2^58, or kNoScale when B is zero, not finite or out of range.
+constexpr int kNoScale = -100000;
+__host__ __device__ __forceinline__ int fixed_scale(double B) {
+  if (!(B > 0.0) || !(B < 1e300)) return kNoScale;
+  const unsigned hi = isum_hi(B);
+  const int e = (int)((hi >> 20) & 0x7FFu) - 1022;   // B < 2^e
+  if (e < -900 || e > 900) return kNoScale;
+  return 58 - e;
+}
+
+// Upper bound of the magnitudes whose high words (sign cleared) have the
+// maximum `hiw`: the double with high word hiw + 1 (0 for hiw == 0).
+__host__ __device__ __forceinline__ double amax_bound(unsigned hiw) {
+  if (hiw == 0) return 0.0;
+  return isum_from_bits((uint64_t)(hiw + 1u) << 32);
+}
+
 // The neighbour sum of a stencil row: fixed point where it applies,
 // otherwise (non-finite or extreme terms) the plain FP64 sum, so that NaN
 // and infinity propagate as in FP64 arithmetic.

@@ -53,6 +53,58 @@ __device__ __forceinline__ double sub_scaled(const Pc& pc, int i, double alpha, 
     return fma(-alpha, pc(i) * v, t);
 }
 
+// w~'_k = M^{-1} w_{k-1} - alpha M^{-1} u_{k-1} of pipe-PR-CG (Algorithm 3)
+// from the row's products u, w and w'_k = w - alpha u.  A Jacobi vector d
+// forms the two explicit products and one FMA; a constant d is factored
+// out, d (w - alpha u) = d w'_k, one multiply: the same quantity
+// reassociated, two FP64 instructions less per row.
+template <class Pc>
+__device__ __forceinline__ double wt_pred(const Pc& pc, int i, double alpha, double u, double w,
+                                          double wp) {
+  if constexpr (std::is_same<Pc, PcScalar>::value) {
+    return pc(0) * wp;
+  } else {
+    const double di = pc(i);
+    return fma(-alpha, di * u, di * w);
+  }
+}
+
+// Scale of the block fixed-point copy of the next p, from upper bounds of
+// the magnitudes it is formed from (thread 0 of a last CTA, after the scalar
+// step).  PR-CG / M-CG: p_{k+1} = r~_{k+1} + beta_{k+1} p_k with
+// r~_{k+1} = r~_k - alpha_k d s_k, so |p_{k+1}| <= max|r~_k| +
+// |alpha_k d| max|s_k| + |beta_{k+1}| max|p_k|.  HS-CG: p_k = d r_k +
+// beta_k p_{k-1}, so |p_k| <= d max|r_k| + |beta_k| max|p_{k-1}|.  A factor
+// 1 + 2^-40 covers the roundings of the bound and of the updates; the
+// trackers are then cleared for the next iteration.
+template <class Pc>
+__device__ __forceinline__ void set_fixed_scale(DevState* S, const Pc& pc, double bound) {
+  const int sc = fixed_scale(bound * (1.0 + 0x1p-40));
+  S->pf_on = (S->pf_allow && !S->done && sc != kNoScale) ? 1 : 0;
+  S->pf_scale = sc;
+  S->pf_bad = 0;
+}
+
+template <class Pc>
+__device__ __forceinline__ void next_fixed_scale_pr(DevState* S, const Pc& pc) {
+  const double d = Pc::on ? pc(0) : 1.0;
+  const double B = amax_bound(S->amax_r) + fabs(S->alpha * d) * amax_bound(S->amax_s) +
+                   fabs(S->beta) * amax_bound(S->amax_p);
+  set_fixed_scale(S, pc, B);
+  S->amax_r = 0u;
+  S->amax_p = 0u;
+  S->amax_s = 0u;
+}
+
+template <class Pc>
+__device__ __forceinline__ void next_fixed_scale_hs(DevState* S, const Pc& pc) {
+  const double d = Pc::on ? pc(0) : 1.0;
+  const double B = d * amax_bound(S->amax_r) + fabs(S->beta) * amax_bound(S->amax_p);
+  set_fixed_scale(S, pc, B);
+  S->amax_r = 0u;
+  S->amax_p = 0u;
+}
+
 // Rows are processed in tiles of kBlock consecutive rows; CTAs stride over
 // tiles so that every CTA's partial sums have a fixed order.
 #define PRCG_ROWS(i, n)                                                         \
@@ -65,7 +117,9 @@ template <class Op, class Pc>
 __global__ void __launch_bounds__(kBlock) k_init_a(Op op, Pc pc, Vecs V, DevState* S,
                                                    double* partials) {
   if (__ldcg(&S->done)) return;
+  constexpr bool kFx = HasFixedRow<Op>::value;
   double acc[3] = {0.0, 0.0, 0.0};
+  unsigned mr = 0u;
   const double* __restrict__ x = V.x;
   PRCG_ROWS(i, op.n) {
     const double ax = op.row(i, [&](int j) { return __ldg(x + j); });
@@ -75,9 +129,14 @@ __global__ void __launch_bounds__(kBlock) k_init_a(Op op, Pc pc, Vecs V, DevStat
     V.r[0][i] = r;
     if (Pc::on) V.rt[0][i] = rt;
     V.p[0][i] = rt;
+    if (kFx) mr = max(mr, mag_hi(rt));
     acc[0] += rt * r;
     acc[1] += r * r;
     acc[2] += bi * bi;
+  }
+  if (kFx) {   // max |r~_0| = max |p_0|, for the scale of the first fixed-point p
+    cta_atomic_max(mr, &S->amax_r);
+    cta_atomic_max(mr, &S->amax_p);
   }
   double tot[3];
   if (grid_sum<3>(acc, partials, S, tot) && threadIdx.x == 0) {
@@ -108,11 +167,14 @@ __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevStat
   const bool pipe = variant == V_PIPE || variant == V_PIPE_M || variant == V_GV ||
                     variant == V_PIPE_NR;
   const bool keep_w = variant == V_CGCG || variant == V_GV || variant == V_PIPE_NR;
+  constexpr bool kFx = HasFixedRow<Op>::value;
   double acc[3] = {0.0, 0.0, 0.0};
+  unsigned ms = 0u;
   const double* __restrict__ p = V.p[0];
   PRCG_ROWS(i, op.n) {
     const double s = op.row(i, [&](int j) { return __ldg(p + j); });
     const double st = Pc::on ? pc(i) * s : s;
+    if (kFx) ms = max(ms, mag_hi(s));
     V.s[0][i] = s;
     if (Pc::on && pipe) V.st[0][i] = st;
     if (keep_w) V.w[0][i] = s;   // w_0 = A r~_0 is the same product (p_0 = r~_0)
@@ -124,6 +186,7 @@ __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevStat
     acc[1] += rt * s;
     acc[2] += st * s;
   }
+  if (kFx) cta_atomic_max(ms, &S->amax_s);
   double tot[3];
   if (grid_sum<3>(acc, partials, S, tot) && threadIdx.x == 0) {
     S->mu = tot[0];
@@ -135,6 +198,8 @@ __global__ void __launch_bounds__(kBlock) k_init_b(Op op, Pc pc, Vecs V, DevStat
     if (variant == V_PR || variant == V_PIPE || variant == V_M || variant == V_PIPE_M ||
         variant == V_PR_NR || variant == V_PIPE_NR) {
       scalar_step_pr(S, variant == V_M || variant == V_PIPE_M);
+      if (kFx && (variant == V_PR || variant == V_M || variant == V_PR_NR))
+        next_fixed_scale_pr(S, pc);
     } else {
       const double nu = S->nu, mu = tot[0];
       if (!finite(nu) || !finite(mu) || !(mu > 0.0) || nu < 0.0) {
@@ -164,10 +229,13 @@ __global__ void __launch_bounds__(kBlock) k_hs_a(Op op, Pc pc, Vecs V, DevState*
   const double* __restrict__ s = V.s[0];
   double* __restrict__ x = V.x;
   constexpr bool kNuDot = Pc::on && !std::is_same<Pc, PcScalar>::value;
+  constexpr bool kFx = HasFixedRow<Op>::value;
+  unsigned mr = 0u;
   auto update = [&](double pi, double si, double& xi, double& ri, double di) {
     xi = fma(alpha, pi, xi);
     const double rn = fma(-alpha, si, ri);
     ri = rn;
+    if (kFx) mr = max(mr, mag_hi(rn));
     acc[1] = fma(rn, rn, acc[1]);
     if (kNuDot) acc[0] = fma(di * rn, rn, acc[0]);
   };
@@ -192,6 +260,7 @@ __global__ void __launch_bounds__(kBlock) k_hs_a(Op op, Pc pc, Vecs V, DevState*
     x[i] = xi;
     r[i] = ri;
   }
+  if (kFx) cta_atomic_max(mr, &S->amax_r);
   double tot[2];
   if (grid_sum<2>(acc, partials, S, tot) && threadIdx.x == 0) {
     const int k = S->k + 1;
@@ -209,18 +278,26 @@ __global__ void __launch_bounds__(kBlock) k_hs_a(Op op, Pc pc, Vecs V, DevState*
         S->beta = nu / S->nu;
         S->nu = nu;
         trace(S, k, TR_BETA, S->beta);
+        if (kFx) next_fixed_scale_hs(S, pc);
       }
     }
   }
 }
 
 // Sweep B of iteration k: p_k = M^{-1} r_k + beta_k p_{k-1} (row-local).
+// For a constant stencil it also stores the block fixed-point copy of p_k
+// (scale chosen by sweep A) and tracks max |p_k|.
 template <class Op, class Pc>
 __global__ void __launch_bounds__(kBlock) k_hs_b(Op op, Pc pc, Vecs V, DevState* S) {
   if (__ldcg(&S->done)) return;
   const double beta = __ldcg(&S->beta);
   double* __restrict__ p = V.p[0];
   const double* __restrict__ r = V.r[0];
+  constexpr bool kFx = HasFixedRow<Op>::value;
+  const bool fx = kFx && __ldcg(&S->pf_on);
+  const int sc = kFx ? __ldcg(&S->pf_scale) : 0;
+  unsigned mp = 0u;
+  bool bad = false;
   // two rows per thread with 16-byte accesses (as in k_pr_a)
   const int n = op.n, npair = n >> 1;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < npair; j += gridDim.x * blockDim.x) {
@@ -231,11 +308,29 @@ __global__ void __launch_bounds__(kBlock) k_hs_b(Op op, Pc pc, Vecs V, DevState*
     p2.x = fma(beta, p2.x, Pc::on ? d2.x * r2.x : r2.x);
     p2.y = fma(beta, p2.y, Pc::on ? d2.y * r2.y : r2.y);
     *reinterpret_cast<double2*>(p + i) = p2;
+    if (kFx) {
+      mp = max(mp, max(mag_hi(p2.x), mag_hi(p2.y)));
+      if (fx) {
+        longlong2 q;
+        q.x = to_fixed(p2.x, sc, bad);
+        q.y = to_fixed(p2.y, sc, bad);
+        *reinterpret_cast<longlong2*>(V.pf + i) = q;
+      }
+    }
   }
   if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
     const int i = n - 1;
     const double ri = __ldg(r + i);
-    p[i] = fma(beta, p[i], Pc::on ? pc(i) * ri : ri);
+    const double pn = fma(beta, p[i], Pc::on ? pc(i) * ri : ri);
+    p[i] = pn;
+    if (kFx) {
+      mp = max(mp, mag_hi(pn));
+      if (fx) V.pf[i] = to_fixed(pn, sc, bad);
+    }
+  }
+  if (kFx) {
+    if (fx && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&S->pf_bad, 1);
+    cta_atomic_max(mp, &S->amax_p);
   }
 }
 
@@ -246,13 +341,31 @@ __global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
   if (__ldcg(&S->done)) return;
   double acc[1] = {0.0};
   const double* __restrict__ p = V.p[0];
-  PRCG_ROWS(i, op.n) {
-    const double sn = op.row(i, [&](int j) { return __ldg(p + j); });
-    V.s[0][i] = sn;
-    acc[0] = fma(__ldg(p + i), sn, acc[0]);
+  bool fixed_done = false;
+  if constexpr (HasFixedRow<Op>::value) {
+    if (__ldcg(&S->pf_on) && !__ldcg(&S->pf_bad)) {
+      // the neighbour sums from the block fixed-point copy of p_k
+      const int sc = __ldcg(&S->pf_scale);
+      const long long* __restrict__ P = V.pf;
+      PRCG_ROWS(i, op.n) {
+        const double pi = __ldg(p + i);
+        const double sn = op.row_fixed(i, pi, P, sc);
+        V.s[0][i] = sn;
+        acc[0] = fma(pi, sn, acc[0]);
+      }
+      fixed_done = true;
+    }
+  }
+  if (!fixed_done) {
+    PRCG_ROWS(i, op.n) {
+      const double sn = op.row(i, [&](int j) { return __ldg(p + j); });
+      V.s[0][i] = sn;
+      acc[0] = fma(__ldg(p + i), sn, acc[0]);
+    }
   }
   double tot[1];
   if (grid_sum<1>(acc, partials, S, tot) && threadIdx.x == 0) {
+    if (fixed_done) ++S->pf_sweeps;
     const double mu = tot[0];
     S->mu = mu;
     trace(S, S->k, TR_MU, mu);
@@ -283,6 +396,13 @@ __global__ void __launch_bounds__(kBlock) k_pr_a(Op op, Pc pc, Vecs V, DevState*
   double* __restrict__ p = V.p[0];
   const double* __restrict__ s = V.s[0];
   double acc[2] = {0.0, 0.0};
+  // constant stencil: max |r~_k|, max |p_k| and the block fixed-point copy
+  // of p_k (scale chosen by the previous reduction) for sweep B
+  constexpr bool kFx = HasFixedRow<Op>::value;
+  const bool fx = kFx && __ldcg(&S->pf_on);
+  const int sc = kFx ? __ldcg(&S->pf_scale) : 0;
+  unsigned mr = 0u, mp = 0u;
+  bool bad = false;
   // the update of one row from its old values; returns rtn and writes x, r, p
   auto update = [&](double si, double pi, double& xi, double& ri, double& rti, double di) {
     xi = fma(alpha, pi, xi);
@@ -295,7 +415,12 @@ __global__ void __launch_bounds__(kBlock) k_pr_a(Op op, Pc pc, Vecs V, DevState*
       acc[0] = fma(rtn, rn, acc[0]);
     }
     acc[1] = fma(rn, rn, acc[1]);
-    return fma(beta, pi, rtn);   // p_k
+    const double pn = fma(beta, pi, rtn);   // p_k
+    if (kFx) {
+      mr = max(mr, mag_hi(rtn));
+      mp = max(mp, mag_hi(pn));
+    }
+    return pn;
   };
   // two rows per thread: 16-byte loads and stores halve the memory requests
   // of this streaming sweep (vectors start on 256-byte boundaries)
@@ -315,14 +440,27 @@ __global__ void __launch_bounds__(kBlock) k_pr_a(Op op, Pc pc, Vecs V, DevState*
     *reinterpret_cast<double2*>(r + i) = r2;
     if (Pc::on) *reinterpret_cast<double2*>(rt + i) = rt2;
     *reinterpret_cast<double2*>(p + i) = pn;
+    if (fx) {
+      longlong2 q;
+      q.x = to_fixed(pn.x, sc, bad);
+      q.y = to_fixed(pn.y, sc, bad);
+      *reinterpret_cast<longlong2*>(V.pf + i) = q;
+    }
   }
   if ((n & 1) && blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
     const int i = n - 1;
     double xi = x[i], ri = r[i], rti = Pc::on ? rt[i] : 0.0;
-    p[i] = update(__ldg(s + i), p[i], xi, ri, rti, Pc::on ? pc(i) : 1.0);
+    const double pn = update(__ldg(s + i), p[i], xi, ri, rti, Pc::on ? pc(i) : 1.0);
+    p[i] = pn;
+    if (fx) V.pf[i] = to_fixed(pn, sc, bad);
     x[i] = xi;
     r[i] = ri;
     if (Pc::on) rt[i] = rti;
+  }
+  if (kFx) {
+    if (fx && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&S->pf_bad, 1);
+    cta_atomic_max(mr, &S->amax_r);
+    cta_atomic_max(mp, &S->amax_p);
   }
   __shared__ double sm[2 * 32];
   block_sum<2>(acc, sm);
@@ -344,18 +482,41 @@ __global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
   const double* __restrict__ p = V.p[0];
   const double* __restrict__ rt = Pc::on ? V.rt[0] : V.r[0];
   double acc[3] = {0.0, 0.0, 0.0};
-  PRCG_ROWS(i, op.n) {
-    const double sn = op.row(i, [&](int j) { return __ldg(p + j); });
+  constexpr bool kFx = HasFixedRow<Op>::value;
+  unsigned ms = 0u;
+  auto sums = [&](int i, double pi, double sn) {
     V.s[0][i] = sn;
-    acc[0] = fma(__ldg(p + i), sn, acc[0]);
+    acc[0] = fma(pi, sn, acc[0]);
     acc[1] = fma(__ldg(rt + i), sn, acc[1]);
     if (std::is_same<Pc, PcVec>::value)
       acc[2] = fma(pc(i) * sn, sn, acc[2]);
     else
       acc[2] = fma(sn, sn, acc[2]);
+    if (kFx) ms = max(ms, mag_hi(sn));
+  };
+  bool fixed_done = false;
+  if constexpr (kFx) {
+    if (__ldcg(&S->pf_on) && !__ldcg(&S->pf_bad)) {
+      // the neighbour sums from the block fixed-point copy of p_k
+      const int sc = __ldcg(&S->pf_scale);
+      const long long* __restrict__ P = V.pf;
+      PRCG_ROWS(i, op.n) {
+        const double pi = __ldg(p + i);
+        sums(i, pi, op.row_fixed(i, pi, P, sc));
+      }
+      fixed_done = true;
+    }
   }
+  if (!fixed_done) {
+    PRCG_ROWS(i, op.n) {
+      const double sn = op.row(i, [&](int j) { return __ldg(p + j); });
+      sums(i, __ldg(p + i), sn);
+    }
+  }
+  if (kFx) cta_atomic_max(ms, &S->amax_s);
   double tot[3];
   if (!grid_sum<3>(acc, partials, S, tot)) return;
+  if (threadIdx.x == 0 && fixed_done) ++S->pf_sweeps;
   // last CTA: add sweep A's partial sums (fixed order)
   double a2[2] = {0.0, 0.0};
   for (int b = threadIdx.x; b < grid_a; b += blockDim.x) {
@@ -374,7 +535,10 @@ __global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
     S->nu = nu;
     S->rho = rho;
     trace_pr_sums(S, k);
-    if (!record_and_test(S, k, rho)) scalar_step_pr(S, meurant != 0);
+    if (!record_and_test(S, k, rho)) {
+      scalar_step_pr(S, meurant != 0);
+      if (kFx) next_fixed_scale_pr(S, pc);
+    }
   }
 }
 
@@ -393,7 +557,6 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
   if (__ldcg(&S->done)) return;
   const double alpha = __ldcg(&S->alpha);
   const double beta = __ldcg(&S->beta);
-  const double ad = std::is_same<Pc, PcScalar>::value ? alpha * pc(0) : 0.0;
   const double* __restrict__ rt_o = Pc::on ? V.rt[qr] : V.r[qr];
   const double* __restrict__ st_o = Pc::on ? V.st[qr] : V.s[qr];
   const double* __restrict__ r_o = V.r[qr];
@@ -411,10 +574,9 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
     const double wp = fma(-alpha, u, w);
     double rtn = rn, sn, stn;
     if (Pc::on) {
-      const double di = pc(i);
       const double sti = __ldg(st_o + i);
       rtn = fma(-alpha, sti, __ldg(rt_o + i));
-      const double wtp = sub_scaled(pc, i, alpha, ad, u, di * w);
+      const double wtp = wt_pred(pc, i, alpha, u, w, wp);
       sn = fma(beta, si, wp);
       stn = fma(beta, sti, wtp);
       V.rt[qw][i] = rtn;

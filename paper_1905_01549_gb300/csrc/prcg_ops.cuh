@@ -222,6 +222,27 @@ struct StencilOp {
     neighbours(i, x, y, z, g, v);
     return fma(cdiag, g(i), -neighbour_sum<2 * DIM>(v));
   }
+  // s_i = c p_i - sum of the neighbours, the sum taken from the block
+  // fixed-point copy P of p (scale S, prcg_isum.cuh): 2*DIM 64-bit integer
+  // adds and one exactly rounded conversion, then the one FP64 FMA.
+  __device__ __forceinline__ double row_fixed(int i, double pi, const long long* __restrict__ P,
+                                              int S) const {
+    int x, y, z;
+    coords(i, x, y, z);
+    const int pl = nx * ny;
+    long long acc = 0;
+    auto nb = [&](bool ok, int j) {
+      const long long v = __ldg(P + (ok ? j : i));
+      acc += ok ? v : 0ll;
+    };
+    if (DIM == 3) nb(z > 0, i - pl);
+    nb(y > 0, i - nx);
+    nb(x > 0, i - 1);
+    nb(x < nx - 1, i + 1);
+    nb(y < ny - 1, i + nx);
+    if (DIM == 3) nb(z < nz - 1, i + pl);
+    return fma(cdiag, pi, -fixed_to_double(acc, S));
+  }
   template <class G>
   __device__ __forceinline__ float row32(int i, G&& g) const {
     float acc = 0.f;
@@ -239,6 +260,12 @@ struct StencilOp {
     a2 = fma(cdiag, g2(i), -neighbour_sum<2 * DIM>(v));
   }
 };
+
+// Operators whose product sweeps can read the block fixed-point copy of p.
+template <class Op>
+struct HasFixedRow : std::false_type {};
+template <int DIM>
+struct HasFixedRow<StencilOp<DIM>> : std::true_type {};
 
 // ------------------------------------------- variable-coefficient stencil
 // A = sum_f c_f (e_a - e_b)(e_a - e_b)^T (+ shift I); diagonal precomputed.

@@ -525,7 +525,6 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         return;
       }
       double a5[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-      const double ad = std::is_same<Pc, PcScalar>::value ? alpha * pc(0) : 0.0;
       PRCG_OWN_ROWS(i, rb) {
         double u, w;
         op.row2(i, [&](int j) { return __ldcg(st_o + j); }, [&](int j) { return __ldcg(rt_o + j); },
@@ -537,10 +536,9 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         const double wp = fma(-alpha, u, w);
         double rtn = rn, sn, stn;
         if (Pc::on) {
-          const double di = pc(i);
           const double sti = st_o[i];
           rtn = fma(-alpha, sti, rt_o[i]);
-          const double wtp = sub_scaled(pc, i, alpha, ad, u, di * w);
+          const double wtp = wt_pred(pc, i, alpha, u, w, wp);
           sn = fma(beta, si, wp);
           stn = fma(beta, sti, wtp);
           V.rt[qw][i] = rtn;

@@ -292,10 +292,9 @@ __global__ void __launch_bounds__(kBlock) k_pipe_tma(SellOp op, Pc pc, Vecs V, D
     const double wp = fma(-alpha, u, w);
     double rtn = rn, sn, stn;
     if (Pc::on) {
-      const double di = pc(i);
       const double sti = __ldg(st_o + i);
       rtn = fma(-alpha, sti, __ldg(rt_o + i));
-      const double wtp = fma(-alpha, di * u, di * w);
+      const double wtp = wt_pred(pc, i, alpha, u, w, wp);
       sn = fma(beta, si, wp);
       stn = fma(beta, sti, wtp);
       V.rt[qw][i] = rtn;

@@ -1,0 +1,134 @@
+"""The block fixed-point copy of p in the constant-stencil product sweeps.
+
+On the graph path (n above the persistent bound, forced here with
+PRCG_PERSIST_MAX=0) HS-CG, PR-CG and M-CG on a constant-coefficient stencil
+store, in the sweep that forms p, a 64-bit fixed-point copy of p with one
+scale per vector, and the product sweep adds the neighbour values with
+integer adds.  Checked here: the sweeps really read the copy (the library's
+counter), the iterates match the oracle (Algorithms 1 and 2) under the
+parity bar and the per-row fixed-point path (PRCG_NO_FIXED_P=1) to 1e-12,
+converged solves stop within one iteration of the oracle, and a right-hand
+side scaled by 2^400 or 2^-400 gives exactly the scaled iterates (the scale
+S moves by exactly -400 or +400, including negative S).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import problems as P
+from gpu_common import ITER_TOL, OracleBand, case, csr_matrix, rel
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = ("hs", "pr", "m", "pr_norecompute")
+ORACLE = {"hs": ("hs", {}), "pr": ("pr", {}), "m": ("m", {}),
+          "pr_norecompute": ("pr", {"recompute_nu": False})}
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1905_01549_gb300 as G
+    return G
+
+
+def _fixed_sweeps(S):
+    from paper_1905_01549_gb300 import binding
+    return binding.prcg_last_fixed_sweeps(S.handle)
+
+
+@pytest.mark.parametrize("name", ["poisson3d_ragged", "shifted2d", "poisson2d_64"])
+@pytest.mark.parametrize("precond", ["none", "jacobi"])
+def test_fixed_p_iterates_match_oracle_and_per_row_path(G, name, precond, monkeypatch):
+    import torch
+    monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    prob = case(name)
+    A = csr_matrix(prob)
+    d = O.jacobi_inverse_diagonal(A) if precond == "jacobi" else None
+    b = torch.from_numpy(prob.b).cuda()
+    xs = {}
+    for env in ("0", "1"):
+        monkeypatch.setenv("PRCG_NO_FIXED_P", env)
+        with G.Solver.from_stencil(prob.dims, diag_shift=prob.shift, precond=precond) as S:
+            for v in VARIANTS:
+                for k in (1, 2, 7, 20):
+                    res = S.solve(b, variant=v, tol=0.0, maxit=k, history=True)
+                    assert res.iters == k
+                    want = (k - 1 if v == "hs" else k) if env == "0" else 0
+                    assert _fixed_sweeps(S) == want, (v, k, env, _fixed_sweeps(S))
+                    xs[(env, v, k)] = (res.x.cpu().numpy(), res.hist)
+    for v in VARIANTS:
+        ov, kw = ORACLE[v]
+        band = OracleBand(ov, A, prob.b, d, 20, **kw)
+        for k in (1, 2, 7, 20):
+            xf, hf = xs[("0", v, k)]
+            xr, _ = xs[("1", v, k)]
+            assert rel(xf, xr) <= 1e-12, (v, k, rel(xf, xr))
+            assert band.determined(k) and band.bar_x(k) <= 1e-7
+            assert band.dist_x(k, xf) <= band.bar_x(k), (v, k, band.dist_x(k, xf))
+            ok, worst = band.hist_ok(k, hf, 1e-9)
+            assert ok, (v, k, worst)
+
+
+@pytest.mark.parametrize("precond", ["none", "jacobi"])
+def test_fixed_p_converged_solves(G, precond, monkeypatch):
+    import torch
+    monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    prob = P.grid_problem((40, 36, 30), "fixed_p_conv")
+    A = csr_matrix(prob)
+    d = O.jacobi_inverse_diagonal(A) if precond == "jacobi" else None
+    b = torch.from_numpy(prob.b).cuda()
+    with G.Solver.from_stencil(prob.dims, precond=precond) as S:
+        for v in ("hs", "pr", "m"):
+            ref = O.solve(v, A, prob.b, d=d, tol=1e-10, maxit=4000)
+            res = S.solve(b, variant=v, tol=1e-10, maxit=4000, true_relres=True)
+            assert res.status == ref.status == O.OK
+            assert abs(res.iters - ref.iters) <= 1, (v, res.iters, ref.iters)
+            assert _fixed_sweeps(S) >= res.iters - 1
+            assert res.true_relres <= 1e-9
+            assert rel(res.x.cpu().numpy(), ref.x) <= 1e-8
+
+
+@pytest.mark.parametrize("shift", [400, -400])
+def test_fixed_p_scale_invariance(G, shift, monkeypatch):
+    """b 2^e gives x 2^e bit for bit: every FP64 operation scales exactly and
+    the fixed-point scale moves by -e, so the integers P_i are unchanged."""
+    import torch
+    monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    prob = case("poisson3d_ragged")
+    with G.Solver.from_stencil(prob.dims, precond="jacobi") as S:
+        for v in ("hs", "pr"):
+            base = S.solve(torch.from_numpy(prob.b).cuda(), variant=v, tol=0.0, maxit=25)
+            n0 = _fixed_sweeps(S)
+            scaled = S.solve(torch.from_numpy(np.ldexp(prob.b, shift)).cuda(), variant=v,
+                             tol=0.0, maxit=25)
+            assert _fixed_sweeps(S) == n0 > 0
+            assert np.array_equal(np.ldexp(base.x.cpu().numpy(), shift), scaled.x.cpu().numpy())
+
+
+def test_fixed_p_edge_cases(G, monkeypatch):
+    """b = 0, maxit 0 and 1, an exact x_0 and a NaN in b on the graph path."""
+    import torch
+    monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    dims = (13, 9, 7)
+    x0 = np.random.default_rng(4).integers(-5, 6, 13 * 9 * 7).astype(np.float64)
+    b = P.stencil_apply(dims, x0)   # integers: r_0 = 0 exactly
+    with G.Solver.from_stencil(dims) as S:
+        for v in ("hs", "pr", "m"):
+            z = torch.ones(x0.size, dtype=torch.float64, device="cuda")
+            res = S.solve(torch.zeros_like(z), x0=z, variant=v, tol=1e-10, maxit=50)
+            assert res.status == G.PRCG_OK and res.iters == 0 and float(z.abs().max()) == 0.0
+            res = S.solve(torch.from_numpy(b).cuda(), x0=torch.from_numpy(x0.copy()).cuda(),
+                          variant=v, tol=1e-12, maxit=50)
+            assert res.status == G.PRCG_OK and res.iters == 0
+            for m in (0, 1):
+                res = S.solve(torch.from_numpy(b + 1.0).cuda(), variant=v, tol=1e-12, maxit=m)
+                assert res.status == G.PRCG_NOT_CONVERGED and res.iters == m
+            bad = b.copy()
+            bad[7] = np.nan
+            res = S.solve(torch.from_numpy(bad).cuda(), variant=v, tol=1e-10, maxit=50)
+            assert res.status == G.PRCG_BREAKDOWN and res.iters == 0
