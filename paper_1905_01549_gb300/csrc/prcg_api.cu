@@ -672,6 +672,20 @@ int copy_in(prcg_ctx* c, void* dst, const void* src, size_t bytes) {
   return PRCG_OK;
 }
 
+// The caller's concatenated face array (x-faces, y-faces, z-faces) into the
+// context's three aligned face arrays.
+int copy_faces(prcg_ctx* c, const OpDesc& op, const double* faces, size_t nfx, size_t nfy,
+               size_t nfz) {
+  int rc;
+  if ((rc = copy_in(c, const_cast<double*>(op.fx), faces, nfx * sizeof(double))) != PRCG_OK)
+    return rc;
+  if ((rc = copy_in(c, const_cast<double*>(op.fy), faces + nfx, nfy * sizeof(double))) != PRCG_OK)
+    return rc;
+  if (nfz)
+    rc = copy_in(c, const_cast<double*>(op.fz), faces + nfx + nfy, nfz * sizeof(double));
+  return rc;
+}
+
 // Test kernel: the stencil operators' neighbour sum over count K-tuples.
 template <int K>
 __global__ void k_test_neighbour_sum(const double* __restrict__ v, int64_t count,
@@ -840,15 +854,18 @@ int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t
     op.kind = dim == 2 ? OP_VC2 : OP_VC3;
     const size_t nfx = (size_t)nz * ny * (nx + 1), nfy = (size_t)nz * (ny + 1) * nx;
     const size_t nfz = dim == 3 ? (size_t)(nz + 1) * ny * nx : 0;
-    const size_t nf = nfx + nfy + nfz;
-    if (cudaMalloc(&c->vpool, (nf + (size_t)n + 2) * sizeof(double)) != cudaSuccess)
+    // each face array and the diagonal start on a 256-byte boundary (the
+    // two-row products load y- and z-faces and diagonals as 16-byte pairs)
+    auto up32 = [](size_t v) { return (v + 31) / 32 * 32; };
+    const size_t ofy = up32(nfx), ofz = ofy + up32(nfy), oad = ofz + up32(nfz);
+    if (cudaMalloc(&c->vpool, (oad + up32((size_t)n) + 2) * sizeof(double)) != cudaSuccess)
       return fail(set_err(c, PRCG_ERR_OOM, "face allocation failed"));
-    if ((rc = wait_user(c)) != PRCG_OK) return fail(rc);
-    if ((rc = copy_in(c, c->vpool, face_coeff, nf * sizeof(double))) != PRCG_OK) return fail(rc);
     op.fx = c->vpool;
-    op.fy = c->vpool + nfx;
-    op.fz = dim == 3 ? c->vpool + nfx + nfy : nullptr;
-    double* adiag = c->vpool + nf;
+    op.fy = c->vpool + ofy;
+    op.fz = dim == 3 ? c->vpool + ofz : nullptr;
+    if ((rc = wait_user(c)) != PRCG_OK) return fail(rc);
+    if ((rc = copy_faces(c, op, face_coeff, nfx, nfy, nfz)) != PRCG_OK) return fail(rc);
+    double* adiag = c->vpool + oad;
     op.adiag = adiag;
     double* d = precond == PRCG_PRECOND_JACOBI ? const_cast<double*>(c->plan.pc.d) : nullptr;
     k_vc_diag<<<c->plan.sms * 4, 256, 0, c->cs>>>(dim, (int)nx, (int)ny, (int)nz, op.fx, op.fy,
@@ -1259,7 +1276,8 @@ int prcg_update_faces(prcg_ctx* c, const double* face_coeff, double diag_shift) 
                     (dim == 3 ? (size_t)(op.nz + 1) * op.ny * op.nx : 0);
   int rc;
   if ((rc = wait_user(c)) != PRCG_OK) return rc;
-  if ((rc = copy_in(c, const_cast<double*>(op.fx), face_coeff, nf * sizeof(double))) != PRCG_OK) return rc;
+  const size_t nfx = (size_t)op.nz * op.ny * (op.nx + 1), nfy = (size_t)op.nz * (op.ny + 1) * op.nx;
+  if ((rc = copy_faces(c, op, face_coeff, nfx, nfy, nf - nfx - nfy)) != PRCG_OK) return rc;
   double* d = c->plan.pc.kind == PC_VEC ? const_cast<double*>(c->plan.pc.d) : nullptr;
   k_vc_diag<<<c->plan.sms * 4, 256, 0, c->cs>>>(dim, op.nx, op.ny, op.nz, op.fx, op.fy, op.fz,
                                                diag_shift, const_cast<double*>(op.adiag), d, c->dbad);

@@ -23,18 +23,18 @@
 namespace prcg {
 
 // CTAs per SM the single-product sweeps ask the register allocator for.
-// The constant stencil's product sweeps are bound by integer issue and
-// memory latency (their neighbour sums run on the integer pipes), so they
-// want every warp slot: 8 CTAs of 256 threads, 32 registers a thread.  0
-// leaves the allocator its own choice (the other operators, and the
-// two-product pipelined sweep, which would spill at 32 registers).
+// The constant stencil's product sweeps are bound by memory latency and,
+// on the per-row path, integer issue, so they want many warps: 6 CTAs of
+// 256 threads, at most 40 registers a thread (the block fixed-point path,
+// which takes two rows a thread, spills at 32).  0 leaves the allocator its
+// own choice (the other operators, and the two-product pipelined sweep).
 template <class Op>
 struct SweepMinBlocks {
   static constexpr int value = 0;
 };
 template <int DIM>
 struct SweepMinBlocks<StencilOp<DIM>> {
-  static constexpr int value = 8;
+  static constexpr int value = 6;
 };
 
 // t - alpha (M^{-1} v)_i: the update of a recurrence for a preconditioned
@@ -347,16 +347,47 @@ __global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
       // the neighbour sums from the block fixed-point copy of p_k
       const int sc = __ldcg(&S->pf_scale);
       const long long* __restrict__ P = V.pf;
-      PRCG_ROWS(i, op.n) {
-        const double pi = __ldg(p + i);
-        const double sn = op.row_fixed(i, pi, P, sc);
-        V.s[0][i] = sn;
-        acc[0] = fma(pi, sn, acc[0]);
+      if ((op.nx & 1) == 0) {
+        // pairs of rows of one x-line, 16-byte accesses (n is even)
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (op.n >> 1);
+             j += gridDim.x * blockDim.x) {
+          const int i = 2 * j;
+          const double2 p2 = __ldg(reinterpret_cast<const double2*>(p + i));
+          const double2 s2 = op.rows2_fixed(i, p2, P, sc);
+          *reinterpret_cast<double2*>(V.s[0] + i) = s2;
+          acc[0] = fma(p2.x, s2.x, acc[0]);
+          acc[0] = fma(p2.y, s2.y, acc[0]);
+        }
+      } else {
+        PRCG_ROWS(i, op.n) {
+          const double pi = __ldg(p + i);
+          const double sn = op.row_fixed(i, pi, P, sc);
+          V.s[0][i] = sn;
+          acc[0] = fma(pi, sn, acc[0]);
+        }
       }
       fixed_done = true;
     }
   }
-  if (!fixed_done) {
+  bool paired = false;
+  if constexpr (HasRows2<Op>::value) {
+    if (!fixed_done && op.pairs_ok()) {
+      // two rows of one grid line per thread, 16-byte loads (n is even)
+      auto g = [&](int j) { return __ldg(p + j); };
+      auto g2 = [&](int j) { return __ldg(reinterpret_cast<const double2*>(p + j)); };
+      for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (op.n >> 1);
+           j += gridDim.x * blockDim.x) {
+        const int i = 2 * j;
+        const double2 s2 = op.rows2(i, g, g2);
+        *reinterpret_cast<double2*>(V.s[0] + i) = s2;
+        const double2 p2 = g2(i);
+        acc[0] = fma(p2.x, s2.x, acc[0]);
+        acc[0] = fma(p2.y, s2.y, acc[0]);
+      }
+      paired = true;
+    }
+  }
+  if (!fixed_done && !paired) {
     PRCG_ROWS(i, op.n) {
       const double sn = op.row(i, [&](int j) { return __ldg(p + j); });
       V.s[0][i] = sn;
@@ -500,14 +531,51 @@ __global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
       // the neighbour sums from the block fixed-point copy of p_k
       const int sc = __ldcg(&S->pf_scale);
       const long long* __restrict__ P = V.pf;
-      PRCG_ROWS(i, op.n) {
-        const double pi = __ldg(p + i);
-        sums(i, pi, op.row_fixed(i, pi, P, sc));
+      static_assert(!std::is_same<Pc, PcVec>::value, "constant stencils have a scalar d");
+      if ((op.nx & 1) == 0) {
+        // pairs of rows of one x-line, 16-byte accesses (n is even)
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (op.n >> 1);
+             j += gridDim.x * blockDim.x) {
+          const int i = 2 * j;
+          const double2 p2 = __ldg(reinterpret_cast<const double2*>(p + i));
+          const double2 s2 = op.rows2_fixed(i, p2, P, sc);
+          *reinterpret_cast<double2*>(V.s[0] + i) = s2;
+          const double2 r2 = __ldg(reinterpret_cast<const double2*>(rt + i));
+          acc[0] = fma(p2.x, s2.x, acc[0]);
+          acc[1] = fma(r2.x, s2.x, acc[1]);
+          acc[2] = fma(s2.x, s2.x, acc[2]);
+          acc[0] = fma(p2.y, s2.y, acc[0]);
+          acc[1] = fma(r2.y, s2.y, acc[1]);
+          acc[2] = fma(s2.y, s2.y, acc[2]);
+          ms = max(ms, max(mag_hi(s2.x), mag_hi(s2.y)));
+        }
+      } else {
+        PRCG_ROWS(i, op.n) {
+          const double pi = __ldg(p + i);
+          sums(i, pi, op.row_fixed(i, pi, P, sc));
+        }
       }
       fixed_done = true;
     }
   }
-  if (!fixed_done) {
+  bool paired = false;
+  if constexpr (HasRows2<Op>::value) {
+    if (!fixed_done && op.pairs_ok()) {
+      // two rows of one grid line per thread, 16-byte loads (n is even)
+      auto g = [&](int j) { return __ldg(p + j); };
+      auto g2 = [&](int j) { return __ldg(reinterpret_cast<const double2*>(p + j)); };
+      for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (op.n >> 1);
+           j += gridDim.x * blockDim.x) {
+        const int i = 2 * j;
+        const double2 s2 = op.rows2(i, g, g2);
+        const double2 p2 = g2(i);
+        sums(i, p2.x, s2.x);
+        sums(i + 1, p2.y, s2.y);
+      }
+      paired = true;
+    }
+  }
+  if (!fixed_done && !paired) {
     PRCG_ROWS(i, op.n) {
       const double sn = op.row(i, [&](int j) { return __ldg(p + j); });
       sums(i, __ldg(p + i), sn);

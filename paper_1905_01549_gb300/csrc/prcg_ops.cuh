@@ -243,6 +243,76 @@ struct StencilOp {
     if (DIM == 3) nb(z < nz - 1, i + pl);
     return fma(cdiag, pi, -fixed_to_double(acc, S));
   }
+  // Rows i and i + 1 of one x-line (i even, nx even; g2(j) loads the pair
+  // j, j + 1 for even j): the pair's own values and its y and z neighbours
+  // with 16-byte loads, the two outer x neighbours alone.  Each row's terms
+  // are neighbours()'s, in its order, so the results equal row()'s bit for
+  // bit.
+  __device__ __forceinline__ bool pairs_ok() const { return (nx & 1) == 0; }
+  template <class G, class G2>
+  __device__ __forceinline__ double2 rows2(int i, G&& g, G2&& g2) const {
+    int x, y, z;
+    coords(i, x, y, z);
+    const int pl = nx * ny;
+    const double2 c = g2(i);
+    const double xl = g(x > 0 ? i - 1 : i), xr = g(x + 2 < nx ? i + 2 : i);
+    const double2 ym = g2(y > 0 ? i - nx : i), yp = g2(y < ny - 1 ? i + nx : i);
+    double2 zm = c, zp = c;
+    if (DIM == 3) {
+      zm = g2(z > 0 ? i - pl : i);
+      zp = g2(z < nz - 1 ? i + pl : i);
+    }
+    double v0[2 * DIM], v1[2 * DIM];
+    int t = 0;
+    if (DIM == 3) {
+      v0[t] = z > 0 ? zm.x : 0.0;
+      v1[t++] = z > 0 ? zm.y : 0.0;
+    }
+    v0[t] = y > 0 ? ym.x : 0.0;
+    v1[t++] = y > 0 ? ym.y : 0.0;
+    v0[t] = x > 0 ? xl : 0.0;
+    v1[t++] = c.x;
+    v0[t] = c.y;
+    v1[t++] = x + 2 < nx ? xr : 0.0;
+    v0[t] = y < ny - 1 ? yp.x : 0.0;
+    v1[t++] = y < ny - 1 ? yp.y : 0.0;
+    if (DIM == 3) {
+      v0[t] = z < nz - 1 ? zp.x : 0.0;
+      v1[t++] = z < nz - 1 ? zp.y : 0.0;
+    }
+    return make_double2(fma(cdiag, c.x, -neighbour_sum<2 * DIM>(v0)),
+                        fma(cdiag, c.y, -neighbour_sum<2 * DIM>(v1)));
+  }
+  // Rows i and i + 1 of one x-line (i even, nx even) from P: their x
+  // neighbours inside the pair come from one 16-byte load of P[i], P[i+1],
+  // the y and z neighbours from 16-byte loads of the neighbouring pairs.
+  // The integer sums are exact, so each row equals row_fixed's bit for bit.
+  __device__ __forceinline__ double2 rows2_fixed(int i, double2 pi, const long long* __restrict__ P,
+                                                 int S) const {
+    int x, y, z;
+    coords(i, x, y, z);
+    const int pl = nx * ny;
+    auto ld2 = [&](bool ok, int j) {
+      const longlong2 v = __ldg(reinterpret_cast<const longlong2*>(P + (ok ? j : i)));
+      return ok ? v : make_longlong2(0ll, 0ll);
+    };
+    const longlong2 c = __ldg(reinterpret_cast<const longlong2*>(P + i));
+    long long a0 = c.y, a1 = c.x;   // row i: P[i+1]; row i+1: P[i]
+    const long long xl = __ldg(P + (x > 0 ? i - 1 : i));
+    const long long xr = __ldg(P + (x + 2 < nx ? i + 2 : i));
+    a0 += x > 0 ? xl : 0ll;
+    a1 += x + 2 < nx ? xr : 0ll;
+    const longlong2 ym = ld2(y > 0, i - nx), yp = ld2(y < ny - 1, i + nx);
+    a0 += ym.x + yp.x;
+    a1 += ym.y + yp.y;
+    if (DIM == 3) {
+      const longlong2 zm = ld2(z > 0, i - pl), zp = ld2(z < nz - 1, i + pl);
+      a0 += zm.x + zp.x;
+      a1 += zm.y + zp.y;
+    }
+    return make_double2(fma(cdiag, pi.x, -fixed_to_double(a0, S)),
+                        fma(cdiag, pi.y, -fixed_to_double(a1, S)));
+  }
   template <class G>
   __device__ __forceinline__ float row32(int i, G&& g) const {
     float acc = 0.f;
@@ -266,6 +336,12 @@ template <class Op>
 struct HasFixedRow : std::false_type {};
 template <int DIM>
 struct HasFixedRow<StencilOp<DIM>> : std::true_type {};
+
+// Operators with a two-row product (rows2: rows i, i + 1 of one grid line).
+template <class Op>
+struct HasRows2 : std::false_type {};
+template <int DIM>
+struct HasRows2<StencilOp<DIM>> : std::true_type {};
 
 // ------------------------------------------- variable-coefficient stencil
 // A = sum_f c_f (e_a - e_b)(e_a - e_b)^T (+ shift I); diagonal precomputed.
@@ -311,6 +387,62 @@ struct VarStencilOp {
     visit(i, [&](int j, double a) { acc = fma(a, g(j), acc); });
     return acc;
   }
+  // Rows i and i + 1 of one x-line (i even, nx even; the face arrays and the
+  // diagonal start on 16-byte boundaries; g2(j) loads the pair j, j + 1 for
+  // even j).  The x-face between the two rows is read once; the y- and
+  // z-faces, the diagonals, the pair's own values and its y and z
+  // neighbours come in 16-byte loads -- 16 load instructions for two rows
+  // instead of 30.  Each row's FMA chain is visit()'s (missing neighbours
+  // as coefficient 0 times the row's own value, the same order), so the
+  // results equal row()'s bit for bit.
+  __device__ __forceinline__ bool pairs_ok() const { return (nx & 1) == 0; }
+  template <class G, class G2>
+  __device__ __forceinline__ double2 rows2(int i, G&& g, G2&& g2) const {
+    const int yz = fast_div(divx, i);
+    const int x = i - yz * nx;
+    const int z = DIM == 3 ? fast_div(divy, yz) : 0;
+    const int y = yz - z * ny;
+    const int pl = nx * ny;
+    auto ld2 = [](const double* q) { return __ldg(reinterpret_cast<const double2*>(q)); };
+    const double* fxr = fx + yz * (nx + 1) + x;
+    const double cx0 = __ldg(fxr), cx1 = __ldg(fxr + 1), cx2 = __ldg(fxr + 2);
+    const double2 cym = ld2(fy + (z * (ny + 1) + y) * nx + x);
+    const double2 cyp = ld2(fy + (z * (ny + 1) + y + 1) * nx + x);
+    double2 czm = make_double2(0.0, 0.0), czp = czm;
+    if (DIM == 3) {
+      czm = ld2(fz + i);
+      czp = ld2(fz + i + pl);
+    }
+    const double2 dg = ld2(adiag + i);
+    const double2 c = g2(i);
+    const double xl = g(x > 0 ? i - 1 : i), xr = g(x + 2 < nx ? i + 2 : i);
+    const double2 ym = g2(y > 0 ? i - nx : i), yp = g2(y < ny - 1 ? i + nx : i);
+    double2 zm = c, zp = c;
+    if (DIM == 3) {
+      zm = g2(z > 0 ? i - pl : i);
+      zp = g2(z < nz - 1 ? i + pl : i);
+    }
+    double a0 = 0.0, a1 = 0.0;
+    if (DIM == 3) {
+      a0 = fma(z > 0 ? -czm.x : 0.0, z > 0 ? zm.x : c.x, a0);
+      a1 = fma(z > 0 ? -czm.y : 0.0, z > 0 ? zm.y : c.y, a1);
+    }
+    a0 = fma(y > 0 ? -cym.x : 0.0, y > 0 ? ym.x : c.x, a0);
+    a1 = fma(y > 0 ? -cym.y : 0.0, y > 0 ? ym.y : c.y, a1);
+    a0 = fma(x > 0 ? -cx0 : 0.0, x > 0 ? xl : c.x, a0);
+    a1 = fma(-cx1, c.x, a1);
+    a0 = fma(dg.x, c.x, a0);
+    a1 = fma(dg.y, c.y, a1);
+    a0 = fma(-cx1, c.y, a0);
+    a1 = fma(x + 2 < nx ? -cx2 : 0.0, x + 2 < nx ? xr : c.y, a1);
+    a0 = fma(y < ny - 1 ? -cyp.x : 0.0, y < ny - 1 ? yp.x : c.x, a0);
+    a1 = fma(y < ny - 1 ? -cyp.y : 0.0, y < ny - 1 ? yp.y : c.y, a1);
+    if (DIM == 3) {
+      a0 = fma(z < nz - 1 ? -czp.x : 0.0, z < nz - 1 ? zp.x : c.x, a0);
+      a1 = fma(z < nz - 1 ? -czp.y : 0.0, z < nz - 1 ? zp.y : c.y, a1);
+    }
+    return make_double2(a0, a1);
+  }
   template <class G>
   __device__ __forceinline__ float row32(int i, G&& g) const {
     float acc = 0.f;
@@ -328,6 +460,9 @@ struct VarStencilOp {
     a2 = c2;
   }
 };
+
+template <int DIM>
+struct HasRows2<VarStencilOp<DIM>> : std::true_type {};
 
 // ------------------------------------------------------------ dense matrix
 // Symmetric dense A (the paper's Section 5 model problem, stored dense to

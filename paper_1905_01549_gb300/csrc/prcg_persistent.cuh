@@ -435,10 +435,27 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         return;
       }
       double c1[1] = {0.0};
-      PRCG_OWN_ROWS(i, rb) {
-        const double sn = op.row(i, [&](int j) { return __ldcg(pp + j); });
-        V.s[0][i] = sn;
-        c1[0] = fma(pp[i], sn, c1[0]);
+      bool paired = false;
+      if constexpr (HasRows2<Op>::value) {
+        if (op.pairs_ok()) {
+          auto g = [&](int j) { return __ldcg(pp + j); };
+          auto g2 = [&](int j) { return __ldcg(reinterpret_cast<const double2*>(pp + j)); };
+          for (int i = rb.begin + 2 * (int)threadIdx.x; i < rb.end; i += 2 * (int)blockDim.x) {
+            const double2 s2 = op.rows2(i, g, g2);
+            *reinterpret_cast<double2*>(V.s[0] + i) = s2;
+            const double2 p2 = *reinterpret_cast<const double2*>(pp + i);
+            c1[0] = fma(p2.x, s2.x, c1[0]);
+            c1[0] = fma(p2.y, s2.y, c1[0]);
+          }
+          paired = true;
+        }
+      }
+      if (!paired) {
+        PRCG_OWN_ROWS(i, rb) {
+          const double sn = op.row(i, [&](int j) { return __ldcg(pp + j); });
+          V.s[0][i] = sn;
+          c1[0] = fma(pp[i], sn, c1[0]);
+        }
       }
       if (!grid_sync_sum<1>(c1, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
             ptrace(S, k, TR_MU, t[0]);
@@ -486,12 +503,36 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         finish(S, k, -4);
         return;
       }
-      PRCG_OWN_ROWS(i, rb) {
-        const double sn = op.row(i, [&](int j) { return __ldcg(pp + j); });
-        V.s[0][i] = sn;
-        a5[2] = fma(pp[i], sn, a5[2]);
-        a5[3] = fma(rtv[i], sn, a5[3]);
-        a5[4] = fma(Pc::on ? pc(i) * sn : sn, sn, a5[4]);
+      bool paired = false;
+      if constexpr (HasRows2<Op>::value) {
+        if (op.pairs_ok()) {
+          // two rows of one grid line per thread (the block starts on a
+          // multiple of 32 rows and n is even)
+          auto g = [&](int j) { return __ldcg(pp + j); };
+          auto g2 = [&](int j) { return __ldcg(reinterpret_cast<const double2*>(pp + j)); };
+          for (int i = rb.begin + 2 * (int)threadIdx.x; i < rb.end; i += 2 * (int)blockDim.x) {
+            const double2 s2 = op.rows2(i, g, g2);
+            *reinterpret_cast<double2*>(V.s[0] + i) = s2;
+            const double2 p2 = *reinterpret_cast<const double2*>(pp + i);
+            const double2 r2 = *reinterpret_cast<const double2*>(rtv + i);
+            a5[2] = fma(p2.x, s2.x, a5[2]);
+            a5[3] = fma(r2.x, s2.x, a5[3]);
+            a5[4] = fma(Pc::on ? pc(i) * s2.x : s2.x, s2.x, a5[4]);
+            a5[2] = fma(p2.y, s2.y, a5[2]);
+            a5[3] = fma(r2.y, s2.y, a5[3]);
+            a5[4] = fma(Pc::on ? pc(i + 1) * s2.y : s2.y, s2.y, a5[4]);
+          }
+          paired = true;
+        }
+      }
+      if (!paired) {
+        PRCG_OWN_ROWS(i, rb) {
+          const double sn = op.row(i, [&](int j) { return __ldcg(pp + j); });
+          V.s[0][i] = sn;
+          a5[2] = fma(pp[i], sn, a5[2]);
+          a5[3] = fma(rtv[i], sn, a5[3]);
+          a5[4] = fma(Pc::on ? pc(i) * sn : sn, sn, a5[4]);
+        }
       }
       if (!grid_sync_sum<5>(a5, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
             ptrace(S, k, TR_NU, Pc::on ? t[0] : t[1]);

@@ -25,13 +25,17 @@ def case(name):
         return P.grid_problem((45, 31), "t_vc2r", sigma=2.0)
     if name == "shifted2d":
         return P.grid_problem((33, 47), "t_sh2", shift=0.05, rhs="uniform")
+    if name == "varcoef3d_even":
+        # even nx: the products take two rows of a grid line per thread
+        return P.grid_problem((20, 11, 7), "t_vc3e", sigma=2.0)
     if name == "poisson3d_nx24":
         # nx a multiple of 4: the FP32 stencil product takes four rows at a time
         return P.grid_problem((24, 13, 11), "t_p3x")
     raise KeyError(name)
 
 
-CASES = ["poisson2d_64", "poisson3d_ragged", "varcoef3d_ragged", "varcoef2d_ragged", "shifted2d"]
+CASES = ["poisson2d_64", "poisson3d_ragged", "varcoef3d_ragged", "varcoef2d_ragged", "shifted2d",
+         "varcoef3d_even"]
 GPU_VARIANTS = ["hs", "pr", "pipe_pr", "m", "pipe_m", "cgcg", "gv"]
 
 

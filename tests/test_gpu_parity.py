@@ -95,11 +95,14 @@ def test_first_20_iterations(G, torch_mod, name, op, precond):
                     continue
                 # x_k is not determined to DETERMINED by FP64 arithmetic (an
                 # unpreconditioned sigma = 2 diffusion case near k = 20): its
-                # A-norm error, which CG minimises, agrees with the oracle
-                # runs' to 1 % (they spread by up to ~5e-3 among themselves)
+                # A-norm error, which CG minimises, lies within the oracle
+                # runs' own spread (up to 7 % among themselves on these
+                # cases), doubled, of the nearest run, and within 1 %
+                # where they agree more closely
                 assert k >= 15, (variant, k, band.spread_x(k))
                 eas = [O.a_norm_error(A, xstar, r.iterates[k][0]) for r in band.runs]
-                assert min(abs(ea - e) / e for e in eas) <= 1e-2, (variant, k, ea, eas)
+                bar_ea = max(1e-2, 2.0 * (max(eas) - min(eas)) / min(eas))
+                assert min(abs(ea - e) / e for e in eas) <= bar_ea, (variant, k, ea, eas)
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -379,3 +382,36 @@ def test_constant_csr_diagonal_runs_as_scalar(G, torch_mod, path, monkeypatch):
         assert S.jacobi_form == "vector"
     with make_solver(G, prob, "csr", "none") as S:
         assert S.jacobi_form == "none"
+
+
+@pytest.mark.parametrize("path", ["persistent", "graph"])
+@pytest.mark.parametrize("dims", [(20, 11, 7), (44, 31)])
+@pytest.mark.parametrize("precond", ["none", "jacobi"])
+def test_two_row_face_stencil_matches_csr_and_oracle(G, torch_mod, path, dims, precond,
+                                                     monkeypatch):
+    """With an even nx the face-coefficient stencil forms two rows of a grid
+    line per thread (one load of the shared x-face, 16-byte loads of the
+    rest).  Each row's FMA chain is the CSR row's, in the same column order
+    with the same coefficients; only the order in which a thread adds its
+    rows into the inner products changes.  So the face stencil and the same
+    matrix as CSR agree to rounding level over the first iterations, and the
+    face stencil matches the oracle under the parity bar."""
+    torch = torch_mod
+    if path == "graph":
+        monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    import problems as P
+    prob = P.grid_problem(dims, "t_pair", sigma=2.0)
+    A = csr_matrix(prob)
+    d = _oracle_d(A, precond)
+    b = torch.from_numpy(prob.b).cuda()
+    with make_solver(G, prob, "csr", precond) as Sc, make_solver(G, prob, "stencil", precond) as Ss:
+        for variant in ("hs", "pr", "m", "cgcg"):
+            for k in (1, 2, 3, 4):
+                xc = Sc.solve(b, variant=variant, tol=0.0, maxit=k).x.cpu().numpy()
+                xs = Ss.solve(b, variant=variant, tol=0.0, maxit=k).x.cpu().numpy()
+                assert rel(xs, xc) <= 1e-14, (variant, k, rel(xs, xc))
+            band = OracleBand(variant, A, prob.b, d, 20)
+            for k in (7, 15, 20):
+                if band.determined(k):
+                    xs = Ss.solve(b, variant=variant, tol=0.0, maxit=k).x.cpu().numpy()
+                    assert band.dist_x(k, xs) <= band.bar_x(k), (variant, k)
