@@ -230,7 +230,7 @@ def make_solver(G, prob, op, precond):
 # Sources that define the TMA-staged SELL product sweep and its launch
 # configuration (the kernel whose DRAM traffic profiles/traffic.json records).
 SWEEP_SOURCES = ("prcg_common.cuh", "prcg_reduce.cuh", "prcg_ops.cuh", "prcg_isum.cuh",
-                 "prcg_tma.cuh", "prcg_launch.cuh", "prcg_inst_csr.cu")
+                 "prcg_tma.cuh", "prcg_launch.cuh", "prcg_inst_csr.cu", "prcg_inst_csr_sc.cu")
 
 
 def kernel_source_hash() -> str:

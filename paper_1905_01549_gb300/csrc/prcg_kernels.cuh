@@ -23,17 +23,29 @@
 namespace prcg {
 
 // CTAs per SM the single-product sweeps ask the register allocator for.
-// The constant stencil's product sweeps are bound by memory latency and,
-// on the per-row path, integer issue, so they want many warps: 6 CTAs of
-// 256 threads, at most 40 registers a thread (the block fixed-point path,
-// which takes two rows a thread, spills at 32).  0 leaves the allocator its
-// own choice (the other operators, and the two-product pipelined sweep).
+// The constant stencil's product sweeps are bound by memory latency: PR's
+// takes two pairs of rows a loop trip so that their loads are in flight
+// together, which needs up to 64 registers (4 CTAs of 256 threads); HS's,
+// one pair a trip at 6 CTAs (40 registers), below.  0 leaves the allocator
+// its own choice (the other operators, and the two-product pipelined
+// sweep).
 template <class Op>
 struct SweepMinBlocks {
   static constexpr int value = 0;
 };
 template <int DIM>
 struct SweepMinBlocks<StencilOp<DIM>> {
+  static constexpr int value = 4;
+};
+
+// HS-CG's product sweep does one inner product a row (PR-CG's three): it
+// gains more from warps than from the two-pair loop trips of PR's sweep.
+template <class Op>
+struct HsProductMinBlocks {
+  static constexpr int value = SweepMinBlocks<Op>::value;
+};
+template <int DIM>
+struct HsProductMinBlocks<StencilOp<DIM>> {
   static constexpr int value = 6;
 };
 
@@ -336,7 +348,7 @@ __global__ void __launch_bounds__(kBlock) k_hs_b(Op op, Pc pc, Vecs V, DevState*
 
 // Sweep C of iteration k: s_k = A p_k, mu_k = <p_k, s_k>; then alpha_k.
 template <class Op, class Pc>
-__global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
+__global__ void __launch_bounds__(kBlock, HsProductMinBlocks<Op>::value)
     k_hs_c(Op op, Pc pc, Vecs V, DevState* S, double* partials) {
   if (__ldcg(&S->done)) return;
   double acc[1] = {0.0};
@@ -533,14 +545,11 @@ __global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
       const long long* __restrict__ P = V.pf;
       static_assert(!std::is_same<Pc, PcVec>::value, "constant stencils have a scalar d");
       if ((op.nx & 1) == 0) {
-        // pairs of rows of one x-line, 16-byte accesses (n is even)
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (op.n >> 1);
-             j += gridDim.x * blockDim.x) {
-          const int i = 2 * j;
-          const double2 p2 = __ldg(reinterpret_cast<const double2*>(p + i));
-          const double2 s2 = op.rows2_fixed(i, p2, P, sc);
-          *reinterpret_cast<double2*>(V.s[0] + i) = s2;
-          const double2 r2 = __ldg(reinterpret_cast<const double2*>(rt + i));
+        // pairs of rows of one x-line, 16-byte accesses (n is even); two
+        // pairs a loop trip, their loads issued together
+        double* __restrict__ sv = V.s[0];
+        const int np = op.n >> 1, str = gridDim.x * blockDim.x;
+        auto pair_sums = [&](double2 p2, double2 r2, double2 s2) {
           acc[0] = fma(p2.x, s2.x, acc[0]);
           acc[1] = fma(r2.x, s2.x, acc[1]);
           acc[2] = fma(s2.x, s2.x, acc[2]);
@@ -548,6 +557,22 @@ __global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
           acc[1] = fma(r2.y, s2.y, acc[1]);
           acc[2] = fma(s2.y, s2.y, acc[2]);
           ms = max(ms, max(mag_hi(s2.x), mag_hi(s2.y)));
+        };
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += 2 * str) {
+          const bool hb = j + str < np;
+          const int ia = 2 * j, ib = hb ? 2 * (j + str) : ia;
+          const double2 pa = __ldg(reinterpret_cast<const double2*>(p + ia));
+          const double2 pb = __ldg(reinterpret_cast<const double2*>(p + ib));
+          const double2 ra = __ldg(reinterpret_cast<const double2*>(rt + ia));
+          const double2 rb = __ldg(reinterpret_cast<const double2*>(rt + ib));
+          const double2 sa = op.rows2_fixed(ia, pa, P, sc);
+          const double2 sb = op.rows2_fixed(ib, pb, P, sc);
+          *reinterpret_cast<double2*>(sv + ia) = sa;
+          pair_sums(pa, ra, sa);
+          if (hb) {
+            *reinterpret_cast<double2*>(sv + ib) = sb;
+            pair_sums(pb, rb, sb);
+          }
         }
       } else {
         PRCG_ROWS(i, op.n) {

@@ -345,6 +345,14 @@ struct HasRows2<StencilOp<DIM>> : std::true_type {};
 
 // ------------------------------------------- variable-coefficient stencil
 // A = sum_f c_f (e_a - e_b)(e_a - e_b)^T (+ shift I); diagonal precomputed.
+
+// -c where `keep`, else +0.0: the sign flip and the mask are done on the
+// bits, on the integer pipes, so no FP64 instruction is spent on them.
+__device__ __forceinline__ double neg_or_zero(bool keep, double c) {
+  return __longlong_as_double((__double_as_longlong(c) ^ (long long)0x8000000000000000ull) &
+                              (keep ? -1ll : 0ll));
+}
+
 template <int DIM>
 struct VarStencilOp {
   int nx, ny, nz, n;
@@ -370,13 +378,15 @@ struct VarStencilOp {
     const double cxp = __ldg(fx + yz * (nx + 1) + x + 1);
     const double cyp = __ldg(fy + (z * (ny + 1) + y + 1) * nx + x);
     const double czp = DIM == 3 ? __ldg(fz + i + pl) : 0.0;
-    if (DIM == 3) f(z > 0 ? i - pl : i, z > 0 ? -czm : 0.0);
-    f(y > 0 ? i - nx : i, y > 0 ? -cym : 0.0);
-    f(x > 0 ? i - 1 : i, x > 0 ? -cxm : 0.0);
+    // off-diagonal coefficients -c_f, zero for a missing neighbour, formed on
+    // the integer pipes
+    if (DIM == 3) f(z > 0 ? i - pl : i, neg_or_zero(z > 0, czm));
+    f(y > 0 ? i - nx : i, neg_or_zero(y > 0, cym));
+    f(x > 0 ? i - 1 : i, neg_or_zero(x > 0, cxm));
     f(i, __ldg(adiag + i));
-    f(x < nx - 1 ? i + 1 : i, x < nx - 1 ? -cxp : 0.0);
-    f(y < ny - 1 ? i + nx : i, y < ny - 1 ? -cyp : 0.0);
-    if (DIM == 3) f(z < nz - 1 ? i + pl : i, z < nz - 1 ? -czp : 0.0);
+    f(x < nx - 1 ? i + 1 : i, neg_or_zero(x < nx - 1, cxp));
+    f(y < ny - 1 ? i + nx : i, neg_or_zero(y < ny - 1, cyp));
+    if (DIM == 3) f(z < nz - 1 ? i + pl : i, neg_or_zero(z < nz - 1, czp));
   }
   // one FMA chain per row: the large sweeps are bound by FP64 issue, so a
   // second accumulator (one more FP64 add per row) would cost more than the
@@ -415,31 +425,34 @@ struct VarStencilOp {
     }
     const double2 dg = ld2(adiag + i);
     const double2 c = g2(i);
-    const double xl = g(x > 0 ? i - 1 : i), xr = g(x + 2 < nx ? i + 2 : i);
+    const double xl = g(x > 0 ? i - 1 : i), xr = g(x + 2 < nx ? i + 2 : i + 1);
     const double2 ym = g2(y > 0 ? i - nx : i), yp = g2(y < ny - 1 ? i + nx : i);
     double2 zm = c, zp = c;
     if (DIM == 3) {
       zm = g2(z > 0 ? i - pl : i);
       zp = g2(z < nz - 1 ? i + pl : i);
     }
+    // a missing neighbour is loaded from the row itself (the clamped index)
+    // with its coefficient masked to zero, as in visit
+    const double ncx1 = neg_or_zero(true, cx1);
     double a0 = 0.0, a1 = 0.0;
     if (DIM == 3) {
-      a0 = fma(z > 0 ? -czm.x : 0.0, z > 0 ? zm.x : c.x, a0);
-      a1 = fma(z > 0 ? -czm.y : 0.0, z > 0 ? zm.y : c.y, a1);
+      a0 = fma(neg_or_zero(z > 0, czm.x), zm.x, a0);
+      a1 = fma(neg_or_zero(z > 0, czm.y), zm.y, a1);
     }
-    a0 = fma(y > 0 ? -cym.x : 0.0, y > 0 ? ym.x : c.x, a0);
-    a1 = fma(y > 0 ? -cym.y : 0.0, y > 0 ? ym.y : c.y, a1);
-    a0 = fma(x > 0 ? -cx0 : 0.0, x > 0 ? xl : c.x, a0);
-    a1 = fma(-cx1, c.x, a1);
+    a0 = fma(neg_or_zero(y > 0, cym.x), ym.x, a0);
+    a1 = fma(neg_or_zero(y > 0, cym.y), ym.y, a1);
+    a0 = fma(neg_or_zero(x > 0, cx0), xl, a0);
+    a1 = fma(ncx1, c.x, a1);
     a0 = fma(dg.x, c.x, a0);
     a1 = fma(dg.y, c.y, a1);
-    a0 = fma(-cx1, c.y, a0);
-    a1 = fma(x + 2 < nx ? -cx2 : 0.0, x + 2 < nx ? xr : c.y, a1);
-    a0 = fma(y < ny - 1 ? -cyp.x : 0.0, y < ny - 1 ? yp.x : c.x, a0);
-    a1 = fma(y < ny - 1 ? -cyp.y : 0.0, y < ny - 1 ? yp.y : c.y, a1);
+    a0 = fma(ncx1, c.y, a0);
+    a1 = fma(neg_or_zero(x + 2 < nx, cx2), xr, a1);
+    a0 = fma(neg_or_zero(y < ny - 1, cyp.x), yp.x, a0);
+    a1 = fma(neg_or_zero(y < ny - 1, cyp.y), yp.y, a1);
     if (DIM == 3) {
-      a0 = fma(z < nz - 1 ? -czp.x : 0.0, z < nz - 1 ? zp.x : c.x, a0);
-      a1 = fma(z < nz - 1 ? -czp.y : 0.0, z < nz - 1 ? zp.y : c.y, a1);
+      a0 = fma(neg_or_zero(z < nz - 1, czp.x), zp.x, a0);
+      a1 = fma(neg_or_zero(z < nz - 1, czp.y), zp.y, a1);
     }
     return make_double2(a0, a1);
   }
