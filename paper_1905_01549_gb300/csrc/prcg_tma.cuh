@@ -6,13 +6,13 @@
 // 128-byte aligned and every size is a multiple of 16 bytes).  One thread
 // moves a whole tile's entries into shared memory with two cp.async.bulk
 // copies completing on a "full" mbarrier; while the CTA computes tile m,
-// tile m+1 is in flight (two stages).  Warps release a stage on its "empty"
-// mbarrier and the copying thread refills it once all have, so warps never
-// meet at a CTA-wide barrier between tiles.  The rows' own vector entries and
-// the gathered columns still go through ordinary loads.  Every wait on an
-// mbarrier is
-// bounded: after kTmaSpinLimit polls the kernel records PRCG_ERR_TIMEOUT in
-// the scalar block, waits (bounded) for its copies in flight and returns.
+// tile m+1 is in flight (two stages; three in the pipelined sweep).  Warps
+// release a stage on its "empty" mbarrier and the copying thread refills it
+// once all have, so warps never meet at a CTA-wide barrier between tiles.
+// The rows' own vector entries and the gathered columns still go through
+// ordinary loads.  Every wait on an mbarrier is bounded: after kTmaSpinLimit
+// polls the kernel records PRCG_ERR_TIMEOUT in the scalar block, waits
+// (bounded) for its copies in flight and returns.
 #pragma once
 
 #include "prcg_kernels.cuh"
@@ -21,16 +21,24 @@ namespace prcg {
 
 constexpr int kTmaRows = kBlock;            // rows per tile (one per thread)
 constexpr int kTmaCap = kTmaRows * 7;       // entries per stage (tiles of <= 7 per row on average)
+// Stages of the copy pipeline: two for the single-product sweeps; three for
+// the pipelined sweep, whose longer per-tile arithmetic (two products and
+// the updates of Algorithm 3) leaves more time to hide -- measured at 256^3:
+// k_pipe_tma 886 -> 850 us with three, while k_pr_b_tma slowed 354 -> 449 us
+// (fewer resident CTAs for the same shared memory).
 constexpr int kTmaStages = 2;
+constexpr int kTmaStagesPipe = 3;
 constexpr long kTmaSpinLimit = 1L << 24;
 
-struct __align__(128) TmaSmem {
-  int col[kTmaStages][kTmaCap];
-  double val[kTmaStages][kTmaCap];
-  unsigned long long bar[kTmaStages];     // "full": the stage's copies have landed
-  unsigned long long empty[kTmaStages];   // every warp is done with the stage
+template <int ST>
+struct __align__(128) TmaSmemT {
+  int col[ST][kTmaCap];
+  double val[ST][kTmaCap];
+  unsigned long long bar[ST];     // "full": the stage's copies have landed
+  unsigned long long empty[ST];   // every warp is done with the stage
   int failed;
 };
+using TmaSmem = TmaSmemT<kTmaStages>;
 
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -86,7 +94,8 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
 }
 
 // Issue the entry copy of `tile` into `stage` (one thread).
-__device__ __forceinline__ void tma_issue(TmaSmem& sm, const SellOp& op, int tile, int stage) {
+template <int ST>
+__device__ __forceinline__ void tma_issue(TmaSmemT<ST>& sm, const SellOp& op, int tile, int stage) {
   const int s0 = tile * (kTmaRows / 32);
   const int nsl = (op.n + 31) / 32;
   const int s1 = min(s0 + kTmaRows / 32, nsl);
@@ -106,14 +115,14 @@ __device__ __forceinline__ void tma_issue(TmaSmem& sm, const SellOp& op, int til
 // arrives on the stage's "empty" barrier; thread 0 refills a stage once
 // every warp has released it, so no warp waits for the slowest one between
 // tiles.  Returns false if a wait timed out (the caller reports the error).
-template <class RowFn>
-__device__ __forceinline__ bool sell_tma_sweep(TmaSmem& sm, const SellOp& op, RowFn&& row) {
+template <int ST, class RowFn>
+__device__ __forceinline__ bool sell_tma_sweep(TmaSmemT<ST>& sm, const SellOp& op, RowFn&& row) {
   const int ntiles = (op.n + kTmaRows - 1) / kTmaRows;
   const int tid = threadIdx.x, lane = tid & 31;
   volatile int* failed = &sm.failed;
-  int issued[kTmaStages] = {0, 0};     // thread 0's bookkeeping of copies per stage
+  int issued[ST] = {};         // thread 0's bookkeeping of copies per stage
   if (tid == 0) {
-    for (int q = 0; q < kTmaStages; ++q) {
+    for (int q = 0; q < ST; ++q) {
       mbar_init(&sm.bar[q]);
       mbar_init(&sm.empty[q], blockDim.x >> 5);
     }
@@ -122,7 +131,7 @@ __device__ __forceinline__ bool sell_tma_sweep(TmaSmem& sm, const SellOp& op, Ro
   }
   __syncthreads();
   if (tid == 0) {
-    for (int q = 0; q < kTmaStages; ++q) {
+    for (int q = 0; q < ST; ++q) {
       const int t = blockIdx.x + q * gridDim.x;
       if (t < ntiles) {
         tma_issue(sm, op, t, q);
@@ -133,8 +142,8 @@ __device__ __forceinline__ bool sell_tma_sweep(TmaSmem& sm, const SellOp& op, Ro
   int consumed = 0;   // tiles whose "full" phase thread 0 has observed
   int m = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++m) {
-    const int stage = m % kTmaStages;
-    const unsigned parity = (unsigned)((m / kTmaStages) & 1);
+    const int stage = m % ST;
+    const unsigned parity = (unsigned)((m / ST) & 1);
     const bool landed = mbar_wait_bounded(&sm.bar[stage], parity);
     const int stop = __shfl_sync(0xffffffffu, lane == 0 ? *failed : 0, 0);
     if (!__all_sync(0xffffffffu, landed) || stop) {   // warp-uniform decision
@@ -157,7 +166,7 @@ __device__ __forceinline__ bool sell_tma_sweep(TmaSmem& sm, const SellOp& op, Ro
     __syncwarp();
     if (lane == 0) mbar_arrive(&sm.empty[stage]);   // this warp is done with the stage
     if (tid == 0) {
-      const int tn = t + kTmaStages * gridDim.x;
+      const int tn = t + ST * gridDim.x;
       if (tn < ntiles) {
         if (mbar_wait_bounded(&sm.empty[stage], parity)) {
           fence_proxy_async();
@@ -173,8 +182,10 @@ __device__ __forceinline__ bool sell_tma_sweep(TmaSmem& sm, const SellOp& op, Ro
   const bool ok = sm.failed == 0;
   if (!ok && tid == 0) {
     // drain (bounded) every copy issued but not yet observed, before exit
-    for (int mm = consumed; mm < issued[0] + issued[1]; ++mm)
-      mbar_wait_bounded(&sm.bar[mm % kTmaStages], (unsigned)((mm / kTmaStages) & 1));
+    int total = 0;
+    for (int q = 0; q < ST; ++q) total += issued[q];
+    for (int mm = consumed; mm < total; ++mm)
+      mbar_wait_bounded(&sm.bar[mm % ST], (unsigned)((mm / ST) & 1));
   }
   __syncthreads();
   return ok;
@@ -270,7 +281,7 @@ template <class Pc>
 __global__ void __launch_bounds__(kBlock) k_pipe_tma(SellOp op, Pc pc, Vecs V, DevState* S,
                                                      double* partials, int qr, int qw, int meurant) {
   if (__ldcg(&S->done)) return;
-  __shared__ TmaSmem sm;
+  __shared__ TmaSmemT<kTmaStagesPipe> sm;
   const double alpha = __ldcg(&S->alpha);
   const double beta = __ldcg(&S->beta);
   const double* __restrict__ rt_o = Pc::on ? V.rt[qr] : V.r[qr];
