@@ -175,8 +175,18 @@ __global__ void k_vc_diag(int dim, int nx, int ny, int nz, const double* fx, con
   }
 }
 
-__global__ void k_fill(double* v, int n, double a) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) v[i] = a;
+// v_i = 0.5 + u_i with u_i in [0, 1) from the SplitMix64 finaliser of i
+// (Steele, Lea and Flood, OOPSLA 2014): a fixed right-hand side with no
+// structure, so that every row of every iterate is nonzero from the first
+// iteration on.
+__global__ void k_fill_hashed(double* v, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    unsigned long long z = (unsigned long long)i + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = 0.5 + (double)(z >> 11) * 0x1p-53;
+  }
 }
 
 // Adjoint gradient of the face coefficients: for x = A^{-1} b and lambda =
@@ -1100,7 +1110,9 @@ int prcg_time_sweeps(prcg_ctx* c, int variant, int reps, float* ms_per_sweep, in
   }
   cudaEvent_t ev[4];
   for (int q = 0; q <= np; ++q) CK(cudaEventCreate(&ev[q]));
-  // b = 1, x_0 = 0 (any right-hand side does the same work)
+  // a fixed unstructured b, x_0 = 0.  (With b = 1 the iterates of a
+  // constant stencil stay exactly zero away from the boundary for the first
+  // iterations, rows whose neighbour sums take the all-zero branch.)
   int rc = PRCG_OK;
   DevState& h = *c->hS;
   memset(&h, 0, sizeof h);
@@ -1113,7 +1125,7 @@ int prcg_time_sweeps(prcg_ctx* c, int variant, int reps, float* ms_per_sweep, in
   double tsum[3] = {0, 0, 0};
   cudaError_t e = cudaMemsetAsync(c->plan.v.x, 0, (size_t)c->n * sizeof(double), c->cs);
   if (e == cudaSuccess) {
-    k_fill<<<c->plan.sms * 4, 256, 0, c->cs>>>(const_cast<double*>(c->plan.v.b), c->n, 1.0);
+    k_fill_hashed<<<c->plan.sms * 4, 256, 0, c->cs>>>(const_cast<double*>(c->plan.v.b), c->n);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->S, &h, sizeof h, cudaMemcpyHostToDevice, c->cs);
