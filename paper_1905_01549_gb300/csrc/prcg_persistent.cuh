@@ -285,6 +285,10 @@ __device__ __forceinline__ bool persist_product(const Op& op, const double* v0, 
 template <class Op, class Pc, int VARIANT>
 __global__ void __launch_bounds__(kPersistThreads, 1)
     k_persist(Op op, Pc pc, Vecs V, DevState* S, double* partials, GridBar* gb, int meurant) {
+  // Jacobi with a constant d (a scalar) or a vector d
+  constexpr bool kScalarD = std::is_same<Pc, PcScalar>::value;
+  constexpr bool kVecD = Pc::on && !kScalarD;
+  constexpr bool kNuDot = kVecD;   // HS: nu_k = <d r_k, r_k> needs its own sum
   const RowBlock rb(op.n);
   // warps that own rows; the others add nothing to the reductions
   const bool wact = rb.begin + (int)(threadIdx.x & ~31u) < rb.end;
@@ -393,11 +397,13 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         x[i] = fma(alpha, V.p[0][i], x[i]);
         const double rn = fma(-alpha, V.s[0][i], V.r[0][i]);
         V.r[0][i] = rn;
-        if (Pc::on) a2[0] = fma(pc(i) * rn, rn, a2[0]);   // unpreconditioned: nu_k = rho_k
+        // nu_k = <d r_k, r_k>: with a constant d, d <r_k, r_k> (no
+        // preconditioner: nu_k = rho_k)
+        if (kNuDot) a2[0] = fma(pc(i) * rn, rn, a2[0]);
         a2[1] = fma(rn, rn, a2[1]);
       }
       if (!grid_sync_sum<2>(a2, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
-            const double nun = Pc::on ? t[0] : t[1];
+            const double nun = kNuDot ? t[0] : (kScalarD ? pc(0) * t[1] : t[1]);
             ptrace(S, k, TR_NU, nun);
             ptrace(S, k, TR_RHO, t[1]);
             q.status = stop_test(S, k, t[1], stop2, maxit);
@@ -517,10 +523,10 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             const double2 r2 = *reinterpret_cast<const double2*>(rtv + i);
             a5[2] = fma(p2.x, s2.x, a5[2]);
             a5[3] = fma(r2.x, s2.x, a5[3]);
-            a5[4] = fma(Pc::on ? pc(i) * s2.x : s2.x, s2.x, a5[4]);
+            a5[4] = fma(kVecD ? pc(i) * s2.x : s2.x, s2.x, a5[4]);
             a5[2] = fma(p2.y, s2.y, a5[2]);
             a5[3] = fma(r2.y, s2.y, a5[3]);
-            a5[4] = fma(Pc::on ? pc(i + 1) * s2.y : s2.y, s2.y, a5[4]);
+            a5[4] = fma(kVecD ? pc(i + 1) * s2.y : s2.y, s2.y, a5[4]);
           }
           paired = true;
         }
@@ -531,7 +537,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
           V.s[0][i] = sn;
           a5[2] = fma(pp[i], sn, a5[2]);
           a5[3] = fma(rtv[i], sn, a5[3]);
-          a5[4] = fma(Pc::on ? pc(i) * sn : sn, sn, a5[4]);
+          a5[4] = fma(kVecD ? pc(i) * sn : sn, sn, a5[4]);
         }
       }
       if (!grid_sync_sum<5>(a5, partials, gb, epoch, wact, o, [&](const double* t, Bcast& q) {
@@ -539,10 +545,12 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
             ptrace(S, k, TR_RHO, t[1]);
             ptrace(S, k, TR_MU, t[2]);
             ptrace(S, k, TR_SIGMA, t[3]);
-            ptrace(S, k, TR_GAMMA, t[4]);
+            // gamma_k = <d s_k, s_k>: a constant d is factored out of the sum
+            const double gam = kScalarD ? pc(0) * t[4] : t[4];
+            ptrace(S, k, TR_GAMMA, gam);
             q.status = stop_test(S, k, t[1], stop2, maxit);
             if (q.status != kRunning) return;
-            pr_scalars(Pc::on ? t[0] : t[1], t[2], t[3], t[4], meurant != 0, q);
+            pr_scalars(Pc::on ? t[0] : t[1], t[2], t[3], gam, meurant != 0, q);
             ptrace_pr_step(S, k, q);
           })) {
         finish(S, k, -4);

@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(kBlock) k_pr_b_tma(SellOp op, Pc pc, Vecs V, D
     V.s[0][i] = sn;
     acc[0] = fma(__ldg(p + i), sn, acc[0]);
     acc[1] = fma(__ldg(rt + i), sn, acc[1]);
-    if (Pc::on)
+    // gamma_k = <d s_k, s_k>; a constant d is factored out of the sum
+    if (std::is_same<Pc, PcVec>::value)
       acc[2] = fma(pc(i) * sn, sn, acc[2]);
     else
       acc[2] = fma(sn, sn, acc[2]);
@@ -269,7 +270,7 @@ __global__ void __launch_bounds__(kBlock) k_pr_b_tma(SellOp op, Pc pc, Vecs V, D
     const int k = S->k + 1;
     S->mu = tot[0];
     S->sigma = tot[1];
-    S->gamma = tot[2];
+    S->gamma = std::is_same<Pc, PcScalar>::value ? pc(0) * tot[2] : tot[2];
     S->nu = nu;
     S->rho = rho;
     trace_pr_sums(S, k);
