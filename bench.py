@@ -102,8 +102,8 @@ def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int, dvec=Non
         return [("k_hs_a", (6 + dv) * V, (5 if jac and dv else 3) * n),
                 ("k_hs_b", (3 + dv) * V, (2 if jac else 1) * n),
                 ("k_hs_c", 2 * V + A, m + n)]
-    # a constant d is a scalar: r~ -= (alpha d) s is one FMA, and pipe-PR's
-    # w~' = d w' one multiply (a vector d: d s formed first; d u, d w and an FMA)
+    # a constant d is a scalar: r~ -= (alpha d) s is one FMA (a vector d forms
+    # d s first); pipe-PR's w~' = d w' is one multiply for either form of d
     if variant in ("pr", "m"):
         if jac:
             return [("k_pr_a", (9 + dv) * V, (7 if dv else 6) * n),
@@ -111,7 +111,7 @@ def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int, dvec=Non
         return [("k_pr_a", 7 * V, 4 * n), ("k_pr_b", 3 * V + A, m + 3 * n)]
     if variant in ("pipe_pr", "pipe_m"):
         if jac:
-            return [("k_pipe", (12 + dv) * V + A, 2 * m + (15 if dv else 13) * n)]
+            return [("k_pipe", (12 + dv) * V + A, 2 * m + 13 * n)]
         return [("k_pipe", 8 * V + A, 2 * m + 9 * n)]
     raise KeyError(variant)
 

@@ -66,19 +66,13 @@ __device__ __forceinline__ double sub_scaled(const Pc& pc, int i, double alpha, 
 }
 
 // w~'_k = M^{-1} w_{k-1} - alpha M^{-1} u_{k-1} of pipe-PR-CG (Algorithm 3)
-// from the row's products u, w and w'_k = w - alpha u.  A Jacobi vector d
-// forms the two explicit products and one FMA; a constant d is factored
-// out, d (w - alpha u) = d w'_k, one multiply: the same quantity
-// reassociated, two FP64 instructions less per row.
+// from the row's products u, w and w'_k = w - alpha u.  M^{-1} = diag(d)
+// is applied row by row, so d_i w_i - alpha d_i u_i = d_i (w_i - alpha u_i)
+// = d_i w'_k: the same quantity reassociated, one multiply instead of the
+// two explicit products and an FMA (two FP64 instructions less per row).
 template <class Pc>
-__device__ __forceinline__ double wt_pred(const Pc& pc, int i, double alpha, double u, double w,
-                                          double wp) {
-  if constexpr (std::is_same<Pc, PcScalar>::value) {
-    return pc(0) * wp;
-  } else {
-    const double di = pc(i);
-    return fma(-alpha, di * u, di * w);
-  }
+__device__ __forceinline__ double wt_pred(const Pc& pc, int i, double wp) {
+  return pc(i) * wp;
 }
 
 // Scale of the block fixed-point copy of the next p, from upper bounds of
@@ -669,7 +663,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
     if (Pc::on) {
       const double sti = __ldg(st_o + i);
       rtn = fma(-alpha, sti, __ldg(rt_o + i));
-      const double wtp = wt_pred(pc, i, alpha, u, w, wp);
+      const double wtp = wt_pred(pc, i, wp);
       sn = fma(beta, si, wp);
       stn = fma(beta, sti, wtp);
       V.rt[qw][i] = rtn;

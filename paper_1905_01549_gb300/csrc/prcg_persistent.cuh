@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(kPersistThreads, 1)
         if (Pc::on) {
           const double sti = st_o[i];
           rtn = fma(-alpha, sti, rt_o[i]);
-          const double wtp = wt_pred(pc, i, alpha, u, w, wp);
+          const double wtp = wt_pred(pc, i, wp);
           sn = fma(beta, si, wp);
           stn = fma(beta, sti, wtp);
           V.rt[qw][i] = rtn;

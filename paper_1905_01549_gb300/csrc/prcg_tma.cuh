@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kBlock) k_pipe_tma(SellOp op, Pc pc, Vecs V, D
     if (Pc::on) {
       const double sti = __ldg(st_o + i);
       rtn = fma(-alpha, sti, __ldg(rt_o + i));
-      const double wtp = wt_pred(pc, i, alpha, u, w, wp);
+      const double wtp = wt_pred(pc, i, wp);
       sn = fma(beta, si, wp);
       stn = fma(beta, sti, wtp);
       V.rt[qw][i] = rtn;
