@@ -767,7 +767,9 @@ def run_reference(args):
         tot += t
         its += k
     value = its / tot
-    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": 1, "steps": args.steps,
+    stands_in = "; the CSR operator stands in for the stencil" if args.op == "stencil" else ""
+    line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": args.gpus,
+            "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": tot * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
@@ -777,8 +779,7 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": "iters/s", "cores": cores, "kind": "oracle",
                              "sample": f"each step: the main loop of {per} {variant.upper()}-CG "
                                        f"iterations of the C oracle (OpenMP, {cores} threads; "
-                                       "initialize() excluded); the CSR operator stands in for "
-                                       "the stencil"},
+                                       f"initialize() excluded){stands_in}"},
             "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
