@@ -855,6 +855,15 @@ int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t
   if (!face_coeff) {
     op.kind = dim == 2 ? OP_ST2 : OP_ST3;
     op.cdiag = 2.0 * dim + diag_shift;
+    // a small integer diagonal (Poisson, or an integer shift): the product
+    // sweeps that read the block fixed-point copy of p form the whole row in
+    // 64-bit integers (|cint P_i| + |sum P_j| < 14 * 2^58)
+    // (PRCG_NO_INT_DIAG=1 keeps the FP64 FMA c p_i - sum)
+    const char* nid = getenv("PRCG_NO_INT_DIAG");
+    const bool int_ok = !(nid && nid[0] == '1');
+    op.cint = (int_ok && op.cdiag >= 1.0 && op.cdiag <= 8.0 && op.cdiag == std::floor(op.cdiag))
+                  ? (int)op.cdiag
+                  : 0;
     c->plan.pc.kind = PC_NONE;
     if (precond == PRCG_PRECOND_JACOBI) {
       c->plan.pc.kind = PC_SCALAR;

@@ -353,25 +353,34 @@ __global__ void __launch_bounds__(kBlock, HsProductMinBlocks<Op>::value)
       // the neighbour sums from the block fixed-point copy of p_k
       const int sc = __ldcg(&S->pf_scale);
       const long long* __restrict__ P = V.pf;
-      if ((op.nx & 1) == 0) {
-        // pairs of rows of one x-line, 16-byte accesses (n is even)
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (op.n >> 1);
-             j += gridDim.x * blockDim.x) {
-          const int i = 2 * j;
-          const double2 p2 = __ldg(reinterpret_cast<const double2*>(p + i));
-          const double2 s2 = op.rows2_fixed(i, p2, P, sc);
-          *reinterpret_cast<double2*>(V.s[0] + i) = s2;
-          acc[0] = fma(p2.x, s2.x, acc[0]);
-          acc[0] = fma(p2.y, s2.y, acc[0]);
+      // kInt: the whole row in integers (an integer diagonal), a separate
+      // loop so that no predicated FMA is issued for it
+      auto sweep = [&](auto kInt) {
+        constexpr bool KI = decltype(kInt)::value;
+        if ((op.nx & 1) == 0) {
+          // pairs of rows of one x-line, 16-byte accesses (n is even)
+          for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (op.n >> 1);
+               j += gridDim.x * blockDim.x) {
+            const int i = 2 * j;
+            const double2 p2 = __ldg(reinterpret_cast<const double2*>(p + i));
+            const double2 s2 = op.template rows2_fixed<KI>(i, p2, P, sc);
+            *reinterpret_cast<double2*>(V.s[0] + i) = s2;
+            acc[0] = fma(p2.x, s2.x, acc[0]);
+            acc[0] = fma(p2.y, s2.y, acc[0]);
+          }
+        } else {
+          PRCG_ROWS(i, op.n) {
+            const double pi = __ldg(p + i);
+            const double sn = op.template row_fixed<KI>(i, pi, P, sc);
+            V.s[0][i] = sn;
+            acc[0] = fma(pi, sn, acc[0]);
+          }
         }
-      } else {
-        PRCG_ROWS(i, op.n) {
-          const double pi = __ldg(p + i);
-          const double sn = op.row_fixed(i, pi, P, sc);
-          V.s[0][i] = sn;
-          acc[0] = fma(pi, sn, acc[0]);
-        }
-      }
+      };
+      if (op.cint)
+        sweep(std::true_type{});
+      else
+        sweep(std::false_type{});
       fixed_done = true;
     }
   }
@@ -538,42 +547,51 @@ __global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
       const int sc = __ldcg(&S->pf_scale);
       const long long* __restrict__ P = V.pf;
       static_assert(!std::is_same<Pc, PcVec>::value, "constant stencils have a scalar d");
-      if ((op.nx & 1) == 0) {
-        // pairs of rows of one x-line, 16-byte accesses (n is even); two
-        // pairs a loop trip, their loads issued together
-        double* __restrict__ sv = V.s[0];
-        const int np = op.n >> 1, str = gridDim.x * blockDim.x;
-        auto pair_sums = [&](double2 p2, double2 r2, double2 s2) {
-          acc[0] = fma(p2.x, s2.x, acc[0]);
-          acc[1] = fma(r2.x, s2.x, acc[1]);
-          acc[2] = fma(s2.x, s2.x, acc[2]);
-          acc[0] = fma(p2.y, s2.y, acc[0]);
-          acc[1] = fma(r2.y, s2.y, acc[1]);
-          acc[2] = fma(s2.y, s2.y, acc[2]);
-          ms = max(ms, max(mag_hi(s2.x), mag_hi(s2.y)));
-        };
-        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += 2 * str) {
-          const bool hb = j + str < np;
-          const int ia = 2 * j, ib = hb ? 2 * (j + str) : ia;
-          const double2 pa = __ldg(reinterpret_cast<const double2*>(p + ia));
-          const double2 pb = __ldg(reinterpret_cast<const double2*>(p + ib));
-          const double2 ra = __ldg(reinterpret_cast<const double2*>(rt + ia));
-          const double2 rb = __ldg(reinterpret_cast<const double2*>(rt + ib));
-          const double2 sa = op.rows2_fixed(ia, pa, P, sc);
-          const double2 sb = op.rows2_fixed(ib, pb, P, sc);
-          *reinterpret_cast<double2*>(sv + ia) = sa;
-          pair_sums(pa, ra, sa);
-          if (hb) {
-            *reinterpret_cast<double2*>(sv + ib) = sb;
-            pair_sums(pb, rb, sb);
+      // kInt: the whole row in integers (an integer diagonal), a separate
+      // loop so that no predicated FMA is issued for it
+      auto sweep = [&](auto kInt) {
+        constexpr bool KI = decltype(kInt)::value;
+        if ((op.nx & 1) == 0) {
+          // pairs of rows of one x-line, 16-byte accesses (n is even); two
+          // pairs a loop trip, their loads issued together
+          double* __restrict__ sv = V.s[0];
+          const int np = op.n >> 1, str = gridDim.x * blockDim.x;
+          auto pair_sums = [&](double2 p2, double2 r2, double2 s2) {
+            acc[0] = fma(p2.x, s2.x, acc[0]);
+            acc[1] = fma(r2.x, s2.x, acc[1]);
+            acc[2] = fma(s2.x, s2.x, acc[2]);
+            acc[0] = fma(p2.y, s2.y, acc[0]);
+            acc[1] = fma(r2.y, s2.y, acc[1]);
+            acc[2] = fma(s2.y, s2.y, acc[2]);
+            ms = max(ms, max(mag_hi(s2.x), mag_hi(s2.y)));
+          };
+          for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < np; j += 2 * str) {
+            const bool hb = j + str < np;
+            const int ia = 2 * j, ib = hb ? 2 * (j + str) : ia;
+            const double2 pa = __ldg(reinterpret_cast<const double2*>(p + ia));
+            const double2 pb = __ldg(reinterpret_cast<const double2*>(p + ib));
+            const double2 ra = __ldg(reinterpret_cast<const double2*>(rt + ia));
+            const double2 rb = __ldg(reinterpret_cast<const double2*>(rt + ib));
+            const double2 sa = op.template rows2_fixed<KI>(ia, pa, P, sc);
+            const double2 sb = op.template rows2_fixed<KI>(ib, pb, P, sc);
+            *reinterpret_cast<double2*>(sv + ia) = sa;
+            pair_sums(pa, ra, sa);
+            if (hb) {
+              *reinterpret_cast<double2*>(sv + ib) = sb;
+              pair_sums(pb, rb, sb);
+            }
+          }
+        } else {
+          PRCG_ROWS(i, op.n) {
+            const double pi = __ldg(p + i);
+            sums(i, pi, op.template row_fixed<KI>(i, pi, P, sc));
           }
         }
-      } else {
-        PRCG_ROWS(i, op.n) {
-          const double pi = __ldg(p + i);
-          sums(i, pi, op.row_fixed(i, pi, P, sc));
-        }
-      }
+      };
+      if (op.cint)
+        sweep(std::true_type{});
+      else
+        sweep(std::false_type{});
       fixed_done = true;
     }
   }

@@ -30,6 +30,7 @@ struct OpDesc {
   const double* fz;
   const double* adiag;   // variable-coefficient diagonal incl. shift
   double cdiag;          // constant-coefficient diagonal 2*dim + shift
+  int cint;              // cdiag when it is an integer in [1, 8], else 0
   const int* sptr;       // SELL-32: first entry of each 32-row slice
   const int* slen;       // SELL-32: entries per row in each slice
   const int* scol;       // SELL-32 column indices, slice-major, row-minor
@@ -155,9 +156,11 @@ template <int DIM>
 struct StencilOp {
   int nx, ny, nz, n;
   double cdiag;
+  int cint;
   FastDiv divx, divy;
   explicit StencilOp(const OpDesc& o)
-      : nx(o.nx), ny(o.ny), nz(o.nz), n(o.n), cdiag(o.cdiag), divx(o.divx), divy(o.divy) {}
+      : nx(o.nx), ny(o.ny), nz(o.nz), n(o.n), cdiag(o.cdiag), cint(o.cint), divx(o.divx),
+        divy(o.divy) {}
   __device__ __forceinline__ void coords(int i, int& x, int& y, int& z) const {
     const int yz = fast_div(divx, i);
     x = i - yz * nx;
@@ -224,7 +227,13 @@ struct StencilOp {
   }
   // s_i = c p_i - sum of the neighbours, the sum taken from the block
   // fixed-point copy P of p (scale S, prcg_isum.cuh): 2*DIM 64-bit integer
-  // adds and one exactly rounded conversion, then the one FP64 FMA.
+  // adds and one exactly rounded conversion, then the one FP64 FMA.  With
+  // kInt (c an integer in [1, 8], cint) the row's own term is taken from P
+  // too: c P_i - sum P_j is exact in 64 bits (|.| < 14 * 2^58) and the row
+  // is one exactly rounded conversion of it, no FP64 instruction; its error
+  // is that of the copy, at most (c + 2*DIM) 2^-(S+1), normwise like the
+  // neighbour sum's.
+  template <bool kInt = false>
   __device__ __forceinline__ double row_fixed(int i, double pi, const long long* __restrict__ P,
                                               int S) const {
     int x, y, z;
@@ -241,6 +250,7 @@ struct StencilOp {
     nb(x < nx - 1, i + 1);
     nb(y < ny - 1, i + nx);
     if (DIM == 3) nb(z < nz - 1, i + pl);
+    if constexpr (kInt) return fixed_to_double((long long)cint * __ldg(P + i) - acc, S);
     return fma(cdiag, pi, -fixed_to_double(acc, S));
   }
   // Rows i and i + 1 of one x-line (i even, nx even; g2(j) loads the pair
@@ -286,7 +296,9 @@ struct StencilOp {
   // Rows i and i + 1 of one x-line (i even, nx even) from P: their x
   // neighbours inside the pair come from one 16-byte load of P[i], P[i+1],
   // the y and z neighbours from 16-byte loads of the neighbouring pairs.
-  // The integer sums are exact, so each row equals row_fixed's bit for bit.
+  // The integer sums are exact, so each row equals row_fixed<kInt>'s bit
+  // for bit.
+  template <bool kInt = false>
   __device__ __forceinline__ double2 rows2_fixed(int i, double2 pi, const long long* __restrict__ P,
                                                  int S) const {
     int x, y, z;
@@ -310,6 +322,9 @@ struct StencilOp {
       a0 += zm.x + zp.x;
       a1 += zm.y + zp.y;
     }
+    if constexpr (kInt)
+      return make_double2(fixed_to_double((long long)cint * c.x - a0, S),
+                          fixed_to_double((long long)cint * c.y - a1, S));
     return make_double2(fma(cdiag, pi.x, -fixed_to_double(a0, S)),
                         fma(cdiag, pi.y, -fixed_to_double(a1, S)));
   }

@@ -4,8 +4,10 @@ On the graph path (n above the persistent bound, forced here with
 PRCG_PERSIST_MAX=0) HS-CG, PR-CG and M-CG on a constant-coefficient stencil
 store, in the sweep that forms p, a 64-bit fixed-point copy of p with one
 scale per vector, and the product sweep adds the neighbour values with
-integer adds.  Checked here: the sweeps really read the copy (the library's
-counter), the iterates match the oracle (Algorithms 1 and 2) under the
+integer adds.  With an integer diagonal c in [1, 8] (Poisson, or an
+integer shift) the product row c P_i - sum P_j is formed entirely in 64-bit
+integers; PRCG_NO_INT_DIAG=1 keeps the FP64 FMA c p_i - sum.  Checked here:
+the sweeps really read the copy (the library's counter), the iterates match the oracle (Algorithms 1 and 2) under the
 parity bar and the per-row fixed-point path (PRCG_NO_FIXED_P=1) to 1e-12,
 converged solves stop within one iteration of the oracle, and a right-hand
 side scaled by 2^400 or 2^-400 gives exactly the scaled iterates (the scale
@@ -132,3 +134,38 @@ def test_fixed_p_edge_cases(G, monkeypatch):
             bad[7] = np.nan
             res = S.solve(torch.from_numpy(bad).cuda(), variant=v, tol=1e-10, maxit=50)
             assert res.status == G.PRCG_BREAKDOWN and res.iters == 0
+
+
+@pytest.mark.parametrize("dims,shift", [((20, 11, 7), 0.0), ((20, 11, 7), 2.0), ((20, 11, 7), 3.0),
+                                        ((21, 10, 6), 1.0), ((34, 18), 0.0), ((33, 17), 4.0)])
+@pytest.mark.parametrize("precond", ["none", "jacobi"])
+def test_integer_diagonal_row(G, dims, shift, precond, monkeypatch):
+    """c = 2 dim + shift: 6, 8 and 7 (3D) and 4 and 8 (2D, 8 at the limit)
+    take the integer row, 9 (3D, shift 3) keeps the FMA; the two forms of
+    the row agree to 1e-12 over 20 iterations and both follow the oracle
+    (Algorithms 1 and 2) within the parity bar."""
+    import torch
+    monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
+    prob = P.grid_problem(dims, "int_diag", shift=shift)
+    A = csr_matrix(prob)
+    d = O.jacobi_inverse_diagonal(A) if precond == "jacobi" else None
+    b = torch.from_numpy(prob.b).cuda()
+    xs = {}
+    for env in ("0", "1"):
+        monkeypatch.setenv("PRCG_NO_INT_DIAG", env)
+        with G.Solver.from_stencil(prob.dims, diag_shift=prob.shift, precond=precond) as S:
+            for v in ("hs", "pr"):
+                for k in (1, 5, 20):
+                    res = S.solve(b, variant=v, tol=0.0, maxit=k, history=True)
+                    assert res.iters == k
+                    assert _fixed_sweeps(S) == (k - 1 if v == "hs" else k)
+                    xs[(env, v, k)] = (res.x.cpu().numpy(), res.hist)
+    for v in ("hs", "pr"):
+        band = OracleBand(v, A, prob.b, d, 20)
+        for k in (1, 5, 20):
+            xi, hi = xs[("0", v, k)]
+            xf, _ = xs[("1", v, k)]
+            assert rel(xi, xf) <= 1e-12, (v, k, rel(xi, xf))
+            assert band.determined(k) and band.dist_x(k, xi) <= band.bar_x(k), (v, k)
+            ok, worst = band.hist_ok(k, hi, 1e-9)
+            assert ok, (v, k, worst)
