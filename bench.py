@@ -79,7 +79,8 @@ def model_bytes(variant: str, op: str, precond: str, n: int, nnz: int, dim: int 
     raise KeyError(variant)
 
 
-def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int, dvec=None):
+def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int, dvec=None,
+                 int_row=False):
     """Per sweep of this library's schedule: (name, DRAM bytes the sweep must
     move, FP64 instructions it must execute), counted per row and x n.
 
@@ -87,13 +88,16 @@ def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int, dvec=Non
     FMA per stored matrix entry, one FMA per vector update and per
     inner-product term, one multiply per use of an explicit M^{-1} v).  A
     constant-coefficient stencil row counts 1: its neighbour sum is formed in
-    fixed point on the integer pipes, leaving the FMA c p_i - sum, so those
-    product sweeps are bound by integer issue, which this model does not
-    count.
+    fixed point on the integer pipes, leaving the FMA c p_i - sum; with
+    `int_row` (an integer diagonal) the single-product sweeps form the whole
+    row in integers and it counts 0.  Integer work is not counted.
     """
     V = 8.0 * n
     A = 12.0 * nnz + 4.0 * (n + 1) if op == "csr" else 0.0
     m = float(nnz) if op == "csr" else 1.0 * n
+    # an integer stencil diagonal: the single-product sweeps (which read the
+    # block fixed-point copy of p) form the row without an FP64 instruction
+    m1 = 0.0 if (int_row and op == "stencil") else m
     if dvec is None:
         dvec = precond == "jacobi" and op == "csr"
     dv = 1.0 if dvec else 0.0   # read of vector d
@@ -101,14 +105,14 @@ def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int, dvec=Non
     if variant == "hs":
         return [("k_hs_a", (6 + dv) * V, (5 if jac and dv else 3) * n),
                 ("k_hs_b", (3 + dv) * V, (2 if jac else 1) * n),
-                ("k_hs_c", 2 * V + A, m + n)]
+                ("k_hs_c", 2 * V + A, m1 + n)]
     # a constant d is a scalar: r~ -= (alpha d) s is one FMA (a vector d forms
     # d s first); pipe-PR's w~' = d w' is one multiply for either form of d
     if variant in ("pr", "m"):
         if jac:
             return [("k_pr_a", (9 + dv) * V, (7 if dv else 6) * n),
-                    ("k_pr_b", (3 + dv) * V + A, m + (4 if dv else 3) * n)]
-        return [("k_pr_a", 7 * V, 4 * n), ("k_pr_b", 3 * V + A, m + 3 * n)]
+                    ("k_pr_b", (3 + dv) * V + A, m1 + (4 if dv else 3) * n)]
+        return [("k_pr_a", 7 * V, 4 * n), ("k_pr_b", 3 * V + A, m1 + 3 * n)]
     if variant in ("pipe_pr", "pipe_m"):
         if jac:
             return [("k_pipe", (12 + dv) * V + A, 2 * m + 13 * n)]
@@ -136,7 +140,8 @@ def sweep_roofline(S, variant, op, precond, n, nnz, reps=20, sm_mhz=None):
     and place the slowest one on both rooflines (HBM bytes, FP64 issue)."""
     from paper_1905_01549_gb300 import binding
     ms = binding.prcg_time_sweeps(S.handle, binding.VARIANT_IDS[variant], reps)
-    models = sweep_models(variant, op, precond, n, nnz, dvec=S.jacobi_form == "vector")
+    models = sweep_models(variant, op, precond, n, nnz, dvec=S.jacobi_form == "vector",
+                          int_row=S.int_diagonal > 0)
     peak_hbm, hbm_src = _peaks()
     peak_fp = fp64_peak(sm_mhz)
     per = []

@@ -293,6 +293,19 @@ int prcg_last_fixed_sweeps(const prcg_ctx* ctx, int64_t* sweeps);
  */
 int prcg_jacobi_form(const prcg_ctx* ctx);
 
+/*
+ * prcg_int_diagonal -- the diagonal c of a constant-coefficient stencil
+ * context when it is an integer in [1, 8] (2*dim plus an integer shift, e.g.
+ * Poisson: 4 in 2D, 6 in 3D), with which the product sweeps that read the
+ * block fixed-point copy of p form each row c P_i - sum_j P_j exactly in
+ * 64-bit integers and round it once (no FP64 instruction; the error is that
+ * of the copy, normwise, see prcg_last_fixed_sweeps).  0 when the diagonal
+ * is not such an integer, the operator is not a constant stencil, or
+ * PRCG_NO_INT_DIAG=1 was set when the context was created (the row is then
+ * the FP64 FMA c p_i - sum).  Negative on a NULL context.
+ */
+int prcg_int_diagonal(const prcg_ctx* ctx);
+
 int prcg_destroy(prcg_ctx* ctx);
 
 /*

@@ -86,6 +86,12 @@ class Solver:
         """How the preconditioner is applied: "none", "scalar" or "vector"."""
         return ("none", "scalar", "vector")[binding.prcg_jacobi_form(self.handle)]
 
+    @property
+    def int_diagonal(self) -> int:
+        """A constant stencil's integer diagonal (1..8) if its fixed-point product
+        rows run in integers, else 0."""
+        return binding.prcg_int_diagonal(self.handle)
+
     def solve(self, b, x0=None, variant: str = "pr", tol: float = 1e-10,
               maxit: Optional[int] = None, history: bool = False,
               true_relres: bool = False, trace: bool = False) -> SolveResult:

@@ -36,7 +36,7 @@ EXPORTS = ("prcg_create_csr", "prcg_create_stencil", "prcg_create_dense", "prcg_
            "prcg_time_sweeps", "prcg_solve_f32_refined", "prcg_update_faces",
            "prcg_grad_faces", "prcg_grad_csr_values",
            "prcg_last_launches", "prcg_destroy", "prcg_last_error", "prcg_n", "prcg_error_anorm",
-           "prcg_jacobi_form", "prcg_last_fixed_sweeps",
+           "prcg_jacobi_form", "prcg_int_diagonal", "prcg_last_fixed_sweeps",
            "prcg_trace_enable", "prcg_trace_get", "prcg_check_guards",
            "prcg_inject_barrier_skip", "prcg_test_neighbour_sum",
            "prcg_pr_solve_stencil_noalloc", "prcg_batched_create", "prcg_batched_configure",
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.prcg_n.restype = ctypes.c_int64
     lib.prcg_jacobi_form.argtypes = [vp]
     lib.prcg_jacobi_form.restype = ctypes.c_int
+    lib.prcg_int_diagonal.argtypes = [vp]
+    lib.prcg_int_diagonal.restype = ctypes.c_int
     lib.prcg_last_fixed_sweeps.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.prcg_last_fixed_sweeps.restype = ctypes.c_int
     lib.prcg_error_anorm.argtypes = [vp, vp, vp, _c_double_p]
@@ -326,6 +328,13 @@ def prcg_last_fixed_sweeps(ctx) -> int:
 def prcg_jacobi_form(ctx) -> int:
     """0 no preconditioner, 1 scalar d, 2 vector d."""
     rc = load().prcg_jacobi_form(ctx)
+    _check(rc if rc < 0 else 0, ctx)
+    return rc
+
+
+def prcg_int_diagonal(ctx) -> int:
+    """The constant stencil's integer diagonal used by the integer product rows, or 0."""
+    rc = load().prcg_int_diagonal(ctx)
     _check(rc if rc < 0 else 0, ctx)
     return rc
 

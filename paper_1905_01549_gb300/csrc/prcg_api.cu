@@ -1389,6 +1389,12 @@ int prcg_jacobi_form(const prcg_ctx* c) {
   return c->plan.pc.kind == PC_SCALAR ? 1 : c->plan.pc.kind == PC_VEC ? 2 : 0;
 }
 
+int prcg_int_diagonal(const prcg_ctx* c) {
+  if (!c) return PRCG_ERR_INVALID;
+  const int k = c->plan.op.kind;
+  return (k == OP_ST2 || k == OP_ST3) ? c->plan.op.cint : 0;
+}
+
 int prcg_destroy(prcg_ctx* c) {
   if (!c) return PRCG_OK;
   if (c->cs) cudaStreamSynchronize(c->cs);

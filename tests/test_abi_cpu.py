@@ -56,6 +56,7 @@ def test_host_side_argument_checks_need_no_gpu(lib):
     assert lib.prcg_destroy(None) == 0
     assert lib.prcg_n(None) == -1
     assert lib.prcg_jacobi_form(None) == -1
+    assert lib.prcg_int_diagonal(None) == -1
     with pytest.raises(binding.PrcgError):
         binding.prcg_create_stencil(5, 4, 4, 4)
 

@@ -154,6 +154,8 @@ def test_integer_diagonal_row(G, dims, shift, precond, monkeypatch):
     for env in ("0", "1"):
         monkeypatch.setenv("PRCG_NO_INT_DIAG", env)
         with G.Solver.from_stencil(prob.dims, diag_shift=prob.shift, precond=precond) as S:
+            c = 2 * len(dims) + shift
+            assert S.int_diagonal == (int(c) if env == "0" and c <= 8 else 0)
             for v in ("hs", "pr"):
                 for k in (1, 5, 20):
                     res = S.solve(b, variant=v, tol=0.0, maxit=k, history=True)
