@@ -125,8 +125,12 @@ int prcg_create_csr(prcg_ctx** out, int64_t n, int64_t nnz,
  * v_i - S_i, where S_i, the sum of the existing neighbours, is formed exactly
  * in 64-bit fixed point and rounded once (see prcg_test_neighbour_sum), then
  * one FP64 FMA; it differs from an FP64 evaluation in the order of the
- * stencil only in rounding, and is the more accurate of the two.  The
- * variable-coefficient product is an FP64 FMA per entry.
+ * stencil only in rounding, and is the more accurate of the two.  On the
+ * graph path of HS-CG, PR-CG and M-CG the product sweep adds the neighbours
+ * from a block fixed-point copy of p instead (prcg_last_fixed_sweeps), and
+ * with an integer diagonal in [1, 8] it forms the whole row in integers
+ * (prcg_int_diagonal).  The variable-coefficient product is an FP64 FMA
+ * per entry.
  */
 int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t nz,
                         const double* face_coeff, double diag_shift, int precond,

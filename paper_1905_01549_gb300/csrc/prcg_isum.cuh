@@ -5,7 +5,9 @@
 // issue while its memory traffic needs only a fraction of that time.  The
 // neighbour sum of a constant-coefficient stencil needs no multiplication:
 // it is formed here exactly in 64-bit fixed point on the integer pipes and
-// rounded once, which leaves the FP64 pipe one FMA (c p_i - sum) per row.
+// rounded once, which leaves the FP64 pipe one FMA (c p_i - sum) per row
+// (none where the row is taken from a block fixed-point copy of p with an
+// integer c, see StencilOp::row_fixed).
 #pragma once
 
 #include <cstdint>
