@@ -85,3 +85,26 @@ def test_binding_variant_ids_match_header():
     for k, v in enum.items():
         assert getattr(binding, k) == v, k
     assert sorted(binding.VARIANT_IDS.values()) == sorted(enum.values())
+
+
+@pytest.mark.parametrize("lang", ["c", "c++"])
+def test_header_compiles_for_c_and_cpp_callers(lib, tmp_path, lang):
+    """include/prcg.h is a plain C header (C99, pedantic, no warnings) that
+    C++ callers can include too; a call through it links against the
+    library."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc" if lang == "c" else "g++")
+    if cc is None:
+        pytest.skip("no host compiler")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "prcg.h"\n'
+                   'int main(void) { return prcg_int_diagonal(0) == -1 ? 0 : 1; }\n')
+    std = ["-std=c99", "-pedantic"] if lang == "c" else ["-std=c++17", "-x", "c++"]
+    lib_dir = os.path.join(ROOT, "paper_1905_01549_gb300")
+    exe = tmp_path / "use_header"
+    r = subprocess.run([cc, *std, "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-o", str(exe), "-L", lib_dir, "-lprcg",
+                        f"-Wl,-rpath,{lib_dir}"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([str(exe)]).returncode == 0
