@@ -368,11 +368,11 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   CK(cudaEventCreate(&c->ev_start));
   CK(cudaEventCreate(&c->ev_init));
   CK(cudaEventCreate(&c->ev_loop));
-  // 19 n-vectors: x, b, t, d, two buffers each of r, r~, p, s, s~, w, u, and
-  // the block fixed-point copy of p (64-bit integers); each starts on a
-  // 256-byte boundary and is followed by a guard band that covers its
-  // rounding up to 32 entries and 32 more words
-  const size_t nv = 19;
+  // 23 n-vectors: x, b, t, d, two buffers each of r, r~, p, s, s~, w, u, and
+  // the block fixed-point copies (64-bit integers) of p and, per buffer, of
+  // r~ and s~; each starts on a 256-byte boundary and is followed by a guard
+  // band that covers its rounding up to 32 entries and 32 more words
+  const size_t nv = 23;
   const size_t nr = ((size_t)n + 31) / 32 * 32, stride = nr + kGuardWords;
   CK(cudaMalloc(&c->pool, (kGuardWords + nv * stride) * sizeof(double)));
   int grc = add_guard(c, c->pool, kGuardWords);
@@ -390,6 +390,10 @@ int ctx_init_common(prcg_ctx* c, void* stream, int n) {
   V.b = take();
   V.t = take();
   V.pf = reinterpret_cast<long long*>(take());
+  for (int bq = 0; bq < 2; ++bq) {
+    V.rtf[bq] = reinterpret_cast<long long*>(take());
+    V.stf[bq] = reinterpret_cast<long long*>(take());
+  }
   double* d = take();
   for (int k = 0; k < 2; ++k) {
     V.r[k] = take();

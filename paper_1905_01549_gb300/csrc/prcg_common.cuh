@@ -59,6 +59,13 @@ struct DevState {
   int pf_bad;            // a value of the copy did not fit its window (fall back)
   unsigned amax_r, amax_p, amax_s;   // high words (sign cleared) of max |r~|, |p|, |s|
   int pf_sweeps;         // product sweeps of this solve that read the fixed-point copy
+  // pipe-PR-CG on a constant stencil: block fixed-point copies of r~ and s~
+  // per buffer q.  pq_on[q]: the sweep that writes buffer q also stores the
+  // copies, with scales pq_scale_r[q], pq_scale_s[q]; pq_bad[q]: a value did
+  // not fit its window.  The sweep that reads buffer q uses the copies when
+  // pq_on[q] && !pq_bad[q].
+  int pq_on[2], pq_bad[2];
+  int pq_scale_r[2], pq_scale_s[2];
 };
 
 // Scalar trace: slot k holds the scalars of iteration k in the oracle's
@@ -88,6 +95,8 @@ struct Vecs {
   double* u[2];
   double* t;             // scratch vector (true residual, GV's t_k)
   long long* pf;         // block fixed-point copy of p (constant stencils)
+  long long* rtf[2];     // pipe-PR-CG: fixed-point copies of r~ and s~ per buffer
+  long long* stf[2];
 };
 
 // FP32 vectors of the mixed-precision inner solve (A d = r in FP32).

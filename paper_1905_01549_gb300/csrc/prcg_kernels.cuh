@@ -648,6 +648,32 @@ __global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
 }
 
 // ---------------------------------------------------------- pipe-PR-CG / pipe-M
+// Scales of the fixed-point copies of r~_{k+1} and s~_{k+1} (thread 0 of the
+// last CTA of sweep k, after the scalar step; q = the buffer sweep k + 1
+// writes).  With M_r, M_s the maxima of |r~_k|, |s~_k| and ||A||_inf the
+// stencil's largest row sum of magnitudes: r~_{k+1} = r~_k - alpha_k s~_k
+// gives |r~_{k+1}| <= M_r + |alpha_k| M_s, and s~_{k+1} = d (w_k - alpha_k
+// u_k) + beta_{k+1} s~_k with w_k = A r~_k, u_k = A s~_k gives |s~_{k+1}| <=
+// d ||A||_inf (M_r + |alpha_k| M_s) + |beta_{k+1}| M_s (d = 1 without a
+// preconditioner, where r~ = r and s~ = s).  The factor 1 + 2^-40 covers
+// the roundings of the bounds and of the updates; a value outside its
+// window still only sets pq_bad (the next sweep then uses per-row sums).
+template <class Pc>
+__device__ __forceinline__ void next_pipe_scales(DevState* S, const Pc& pc, double anorm, int q) {
+  const double d = Pc::on ? pc(0) : 1.0;
+  const double Ms = amax_bound(S->amax_s);
+  const double Br = amax_bound(S->amax_r) + fabs(S->alpha) * Ms;
+  const double Bs = d * anorm * Br + fabs(S->beta) * Ms;
+  const int sr = fixed_scale(Br * (1.0 + 0x1p-40));
+  const int ss = fixed_scale(Bs * (1.0 + 0x1p-40));
+  S->pq_on[q] = (S->pf_allow && !S->done && sr != kNoScale && ss != kNoScale) ? 1 : 0;
+  S->pq_scale_r[q] = sr;
+  S->pq_scale_s[q] = ss;
+  S->pq_bad[q] = 0;
+  S->amax_r = 0u;
+  S->amax_s = 0u;
+}
+
 // One sweep per iteration k >= 1.  For row i it first forms
 //   u_{k-1} = A s~_{k-1},  w_{k-1} = A r~_{k-1}      (the recomputed w)
 // from the stored s~_{k-1}, r~_{k-1} (buffer qr), then Algorithm 3's updates
@@ -656,10 +682,19 @@ __global__ void __launch_bounds__(kBlock, SweepMinBlocks<Op>::value)
 //   s~_k = w~'_k + beta s~_{k-1}
 // (r~_k, s~_k to buffer qw) and the inner products mu, sigma, gamma, nu of
 // iteration k; u and w never leave registers.
+//
+// Constant stencil: the previous sweep also stored block fixed-point copies
+// of r~ and s~ (one scale per vector, prcg_isum.cuh) beside the FP64
+// vectors, and both products add the neighbours from them with integer
+// adds -- with an integer diagonal the whole row (row_fixed<true>), no FP64
+// instruction.  Rows go in pairs of one x-line with 16-byte accesses where
+// nx is even.  The first two sweeps, and a sweep whose copy had a value
+// outside its window, use the per-row exact sums instead.
 template <class Op, class Pc>
 __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState* S,
                                                  double* partials, int qr, int qw, int meurant) {
   if (__ldcg(&S->done)) return;
+  constexpr bool kFx = HasFixedRow<Op>::value;
   const double alpha = __ldcg(&S->alpha);
   const double beta = __ldcg(&S->beta);
   const double* __restrict__ rt_o = Pc::on ? V.rt[qr] : V.r[qr];
@@ -669,36 +704,148 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
   double* __restrict__ x = V.x;
   double* __restrict__ p = V.p[0];
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-  PRCG_ROWS(i, op.n) {
-    double u, w;
-    op.row2(i, [&](int j) { return __ldg(st_o + j); }, [&](int j) { return __ldg(rt_o + j); },
-            u, w);
-    const double si = __ldg(s_o + i);
-    x[i] = fma(alpha, p[i], x[i]);
-    const double rn = fma(-alpha, si, __ldg(r_o + i));
+  // fixed-point copies: read from buffer qr, written to buffer qw
+  const bool rd_fx = kFx && __ldcg(&S->pq_on[qr]) && !__ldcg(&S->pq_bad[qr]);
+  const bool wr_fx = kFx && __ldcg(&S->pq_on[qw]);
+  const int sr_rd = kFx ? __ldcg(&S->pq_scale_r[qr]) : 0;
+  const int ss_rd = kFx ? __ldcg(&S->pq_scale_s[qr]) : 0;
+  const int sr_wr = kFx ? __ldcg(&S->pq_scale_r[qw]) : 0;
+  const int ss_wr = kFx ? __ldcg(&S->pq_scale_s[qw]) : 0;
+  const long long* __restrict__ rf_rd = V.rtf[qr];
+  const long long* __restrict__ sf_rd = V.stf[qr];
+  unsigned mr = 0u, ms = 0u;
+  bool bad = false;
+  // Algorithm 3's updates of row i from its old values and the two products
+  auto step = [&](int i, double u, double w, double si, double ri, double rti, double sti,
+                  double& xi, double& pi, double& rn, double& sn, double& rtn, double& stn) {
+    xi = fma(alpha, pi, xi);
+    rn = fma(-alpha, si, ri);
     const double wp = fma(-alpha, u, w);
-    double rtn = rn, sn, stn;
+    sn = fma(beta, si, wp);
     if (Pc::on) {
-      const double sti = __ldg(st_o + i);
-      rtn = fma(-alpha, sti, __ldg(rt_o + i));
-      const double wtp = wt_pred(pc, i, wp);
-      sn = fma(beta, si, wp);
-      stn = fma(beta, sti, wtp);
-      V.rt[qw][i] = rtn;
-      V.st[qw][i] = stn;
+      rtn = fma(-alpha, sti, rti);
+      stn = fma(beta, sti, wt_pred(pc, i, wp));
     } else {
-      sn = fma(beta, si, wp);
+      rtn = rn;
       stn = sn;
     }
-    const double pn = fma(beta, p[i], rtn);
-    p[i] = pn;
-    V.r[qw][i] = rn;
-    V.s[qw][i] = sn;
-    acc[0] = fma(pn, sn, acc[0]);
+    pi = fma(beta, pi, rtn);
+    acc[0] = fma(pi, sn, acc[0]);
     acc[1] = fma(rtn, sn, acc[1]);
     acc[2] = fma(stn, sn, acc[2]);
     if (Pc::on) acc[3] = fma(rtn, rn, acc[3]);   // unpreconditioned: nu_k = rho_k
     acc[4] = fma(rn, rn, acc[4]);
+    if (kFx) {
+      mr = max(mr, mag_hi(rtn));
+      ms = max(ms, mag_hi(stn));
+    }
+  };
+  bool done_rows = false;
+  if constexpr (kFx) {
+    // kRd: the products from the copies; kInt: with an integer diagonal
+    // (separate loops, so that no predicated FP64 instruction issues)
+    auto sweep = [&](auto kRd, auto kInt) {
+      constexpr bool RD = decltype(kRd)::value, KI = decltype(kInt)::value;
+      if (op.pairs_ok()) {
+        auto ld2 = [](const double* q, int j) {
+          return __ldg(reinterpret_cast<const double2*>(q + j));
+        };
+        for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < (op.n >> 1);
+             j += gridDim.x * blockDim.x) {
+          const int i = 2 * j;
+          const double2 rt2 = ld2(rt_o, i), st2 = ld2(st_o, i);
+          double2 u2, w2;
+          if constexpr (RD) {
+            u2 = op.template rows2_fixed<KI>(i, st2, sf_rd, ss_rd);
+            w2 = op.template rows2_fixed<KI>(i, rt2, rf_rd, sr_rd);
+          } else {
+            u2 = op.rows2(i, [&](int c) { return __ldg(st_o + c); },
+                          [&](int c) { return ld2(st_o, c); });
+            w2 = op.rows2(i, [&](int c) { return __ldg(rt_o + c); },
+                          [&](int c) { return ld2(rt_o, c); });
+          }
+          const double2 s2 = ld2(s_o, i), r2 = ld2(r_o, i);
+          double2 x2 = *reinterpret_cast<const double2*>(x + i);
+          double2 p2 = *reinterpret_cast<const double2*>(p + i);
+          double2 rn, sn, rtn, stn;
+          step(i, u2.x, w2.x, s2.x, r2.x, rt2.x, st2.x, x2.x, p2.x, rn.x, sn.x, rtn.x, stn.x);
+          step(i + 1, u2.y, w2.y, s2.y, r2.y, rt2.y, st2.y, x2.y, p2.y, rn.y, sn.y, rtn.y,
+               stn.y);
+          *reinterpret_cast<double2*>(x + i) = x2;
+          *reinterpret_cast<double2*>(p + i) = p2;
+          *reinterpret_cast<double2*>(V.r[qw] + i) = rn;
+          *reinterpret_cast<double2*>(V.s[qw] + i) = sn;
+          if (Pc::on) {
+            *reinterpret_cast<double2*>(V.rt[qw] + i) = rtn;
+            *reinterpret_cast<double2*>(V.st[qw] + i) = stn;
+          }
+          if (wr_fx) {
+            longlong2 fr, fs;
+            fr.x = to_fixed(rtn.x, sr_wr, bad);
+            fr.y = to_fixed(rtn.y, sr_wr, bad);
+            fs.x = to_fixed(stn.x, ss_wr, bad);
+            fs.y = to_fixed(stn.y, ss_wr, bad);
+            *reinterpret_cast<longlong2*>(V.rtf[qw] + i) = fr;
+            *reinterpret_cast<longlong2*>(V.stf[qw] + i) = fs;
+          }
+        }
+      } else {
+        PRCG_ROWS(i, op.n) {
+          const double rti = __ldg(rt_o + i), sti = __ldg(st_o + i);
+          double u, w;
+          if constexpr (RD) {
+            u = op.template row_fixed<KI>(i, sti, sf_rd, ss_rd);
+            w = op.template row_fixed<KI>(i, rti, rf_rd, sr_rd);
+          } else {
+            op.row2(i, [&](int j) { return __ldg(st_o + j); },
+                    [&](int j) { return __ldg(rt_o + j); }, u, w);
+          }
+          double xi = x[i], pi = p[i], rn, sn, rtn, stn;
+          step(i, u, w, __ldg(s_o + i), __ldg(r_o + i), rti, sti, xi, pi, rn, sn, rtn, stn);
+          x[i] = xi;
+          p[i] = pi;
+          V.r[qw][i] = rn;
+          V.s[qw][i] = sn;
+          if (Pc::on) {
+            V.rt[qw][i] = rtn;
+            V.st[qw][i] = stn;
+          }
+          if (wr_fx) {
+            V.rtf[qw][i] = to_fixed(rtn, sr_wr, bad);
+            V.stf[qw][i] = to_fixed(stn, ss_wr, bad);
+          }
+        }
+      }
+    };
+    if (!rd_fx)
+      sweep(std::false_type{}, std::false_type{});
+    else if (op.cint)
+      sweep(std::true_type{}, std::true_type{});
+    else
+      sweep(std::true_type{}, std::false_type{});
+    if (wr_fx && __any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+      atomicOr(&S->pq_bad[qw], 1);
+    cta_atomic_max(mr, &S->amax_r);
+    cta_atomic_max(ms, &S->amax_s);
+    done_rows = true;
+  }
+  if (!done_rows) {
+    PRCG_ROWS(i, op.n) {
+      double u, w;
+      op.row2(i, [&](int j) { return __ldg(st_o + j); }, [&](int j) { return __ldg(rt_o + j); },
+              u, w);
+      double xi = x[i], pi = p[i], rn, sn, rtn, stn;
+      step(i, u, w, __ldg(s_o + i), __ldg(r_o + i), __ldg(rt_o + i), __ldg(st_o + i), xi, pi, rn,
+           sn, rtn, stn);
+      x[i] = xi;
+      p[i] = pi;
+      V.r[qw][i] = rn;
+      V.s[qw][i] = sn;
+      if (Pc::on) {
+        V.rt[qw][i] = rtn;
+        V.st[qw][i] = stn;
+      }
+    }
   }
   double tot[5];
   if (grid_sum<5>(acc, partials, S, tot) && threadIdx.x == 0) {
@@ -708,8 +855,12 @@ __global__ void __launch_bounds__(kBlock) k_pipe(Op op, Pc pc, Vecs V, DevState*
     S->gamma = tot[2];
     S->nu = Pc::on ? tot[3] : tot[4];
     S->rho = tot[4];
+    if (kFx && rd_fx) ++S->pf_sweeps;
     trace_pr_sums(S, k);
-    if (!record_and_test(S, k, tot[4])) scalar_step_pr(S, meurant != 0);
+    if (!record_and_test(S, k, tot[4])) {
+      scalar_step_pr(S, meurant != 0);
+      if constexpr (kFx) next_pipe_scales(S, pc, op.anorm_inf(), qr);
+    }
   }
 }
 

@@ -167,6 +167,8 @@ struct StencilOp {
     z = DIM == 3 ? fast_div(divy, yz) : 0;
     y = yz - z * ny;
   }
+  // ||A||_inf = max_i sum_j |a_ij| <= |cdiag| + 2*DIM
+  __device__ __forceinline__ double anorm_inf() const { return fabs(cdiag) + 2.0 * DIM; }
   // f(j, coefficient) for the 2*DIM+1 entries in increasing column order.
   // Missing neighbours (Dirichlet boundary) are visited as column i with
   // coefficient 0, so every load is issued unconditionally.

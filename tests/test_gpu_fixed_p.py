@@ -4,10 +4,12 @@ On the graph path (n above the persistent bound, forced here with
 PRCG_PERSIST_MAX=0) HS-CG, PR-CG and M-CG on a constant-coefficient stencil
 store, in the sweep that forms p, a 64-bit fixed-point copy of p with one
 scale per vector, and the product sweep adds the neighbour values with
-integer adds.  With an integer diagonal c in [1, 8] (Poisson, or an
+integer adds.  pipe-PR-CG and pipe-M-CG do the same with copies of r~
+and s~ (one pair per buffer; their first two sweeps use the per-row sums).
+With an integer diagonal c in [1, 8] (Poisson, or an
 integer shift) the product row c P_i - sum P_j is formed entirely in 64-bit
 integers; PRCG_NO_INT_DIAG=1 keeps the FP64 FMA c p_i - sum.  Checked here:
-the sweeps really read the copy (the library's counter), the iterates match the oracle (Algorithms 1 and 2) under the
+the sweeps really read the copy (the library's counter), the iterates match the oracle (Algorithms 1, 2 and 3) under the
 parity bar and the per-row fixed-point path (PRCG_NO_FIXED_P=1) to 1e-12,
 converged solves stop within one iteration of the oracle, and a right-hand
 side scaled by 2^400 or 2^-400 gives exactly the scaled iterates (the scale
@@ -22,9 +24,21 @@ from gpu_common import ITER_TOL, OracleBand, case, csr_matrix, rel
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ("hs", "pr", "m", "pr_norecompute")
+VARIANTS = ("hs", "pr", "m", "pr_norecompute", "pipe_pr", "pipe_m")
 ORACLE = {"hs": ("hs", {}), "pr": ("pr", {}), "m": ("m", {}),
-          "pr_norecompute": ("pr", {"recompute_nu": False})}
+          "pr_norecompute": ("pr", {"recompute_nu": False}),
+          "pipe_pr": ("pipe_pr", {}), "pipe_m": ("pipe_m", {})}
+
+
+def _want_fixed(v, k):
+    """Product sweeps of a k-iteration solve that read a fixed-point copy:
+    HS-CG forms p_k after its first product; the pipelined sweeps store the
+    copies from their second sweep on and read them from their third."""
+    if v == "hs":
+        return k - 1
+    if v.startswith("pipe"):
+        return max(0, k - 2)
+    return k
 
 
 @pytest.fixture(scope="module")
@@ -60,7 +74,7 @@ def test_fixed_p_iterates_match_oracle_and_per_row_path(G, name, precond, monkey
                 for k in (1, 2, 7, 20):
                     res = S.solve(b, variant=v, tol=0.0, maxit=k, history=True)
                     assert res.iters == k
-                    want = (k - 1 if v == "hs" else k) if env == "0" else 0
+                    want = _want_fixed(v, k) if env == "0" else 0
                     assert _fixed_sweeps(S) == want, (v, k, env, _fixed_sweeps(S))
                     xs[(env, v, k)] = (res.x.cpu().numpy(), res.hist)
     for v in VARIANTS:
@@ -85,12 +99,12 @@ def test_fixed_p_converged_solves(G, precond, monkeypatch):
     d = O.jacobi_inverse_diagonal(A) if precond == "jacobi" else None
     b = torch.from_numpy(prob.b).cuda()
     with G.Solver.from_stencil(prob.dims, precond=precond) as S:
-        for v in ("hs", "pr", "m"):
+        for v in ("hs", "pr", "m", "pipe_pr"):
             ref = O.solve(v, A, prob.b, d=d, tol=1e-10, maxit=4000)
             res = S.solve(b, variant=v, tol=1e-10, maxit=4000, true_relres=True)
             assert res.status == ref.status == O.OK
             assert abs(res.iters - ref.iters) <= 1, (v, res.iters, ref.iters)
-            assert _fixed_sweeps(S) >= res.iters - 1
+            assert _fixed_sweeps(S) >= res.iters - 2
             assert res.true_relres <= 1e-9
             assert rel(res.x.cpu().numpy(), ref.x) <= 1e-8
 
@@ -103,7 +117,7 @@ def test_fixed_p_scale_invariance(G, shift, monkeypatch):
     monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
     prob = case("poisson3d_ragged")
     with G.Solver.from_stencil(prob.dims, precond="jacobi") as S:
-        for v in ("hs", "pr"):
+        for v in ("hs", "pr", "pipe_pr"):
             base = S.solve(torch.from_numpy(prob.b).cuda(), variant=v, tol=0.0, maxit=25)
             n0 = _fixed_sweeps(S)
             scaled = S.solve(torch.from_numpy(np.ldexp(prob.b, shift)).cuda(), variant=v,
@@ -120,7 +134,7 @@ def test_fixed_p_edge_cases(G, monkeypatch):
     x0 = np.random.default_rng(4).integers(-5, 6, 13 * 9 * 7).astype(np.float64)
     b = P.stencil_apply(dims, x0)   # integers: r_0 = 0 exactly
     with G.Solver.from_stencil(dims) as S:
-        for v in ("hs", "pr", "m"):
+        for v in ("hs", "pr", "m", "pipe_pr"):
             z = torch.ones(x0.size, dtype=torch.float64, device="cuda")
             res = S.solve(torch.zeros_like(z), x0=z, variant=v, tol=1e-10, maxit=50)
             assert res.status == G.PRCG_OK and res.iters == 0 and float(z.abs().max()) == 0.0
@@ -143,7 +157,7 @@ def test_integer_diagonal_row(G, dims, shift, precond, monkeypatch):
     """c = 2 dim + shift: 6, 8 and 7 (3D) and 4 and 8 (2D, 8 at the limit)
     take the integer row, 9 (3D, shift 3) keeps the FMA; the two forms of
     the row agree to 1e-12 over 20 iterations and both follow the oracle
-    (Algorithms 1 and 2) within the parity bar."""
+    (Algorithms 1, 2 and 3) within the parity bar."""
     import torch
     monkeypatch.setenv("PRCG_PERSIST_MAX", "0")
     prob = P.grid_problem(dims, "int_diag", shift=shift)
@@ -156,13 +170,13 @@ def test_integer_diagonal_row(G, dims, shift, precond, monkeypatch):
         with G.Solver.from_stencil(prob.dims, diag_shift=prob.shift, precond=precond) as S:
             c = 2 * len(dims) + shift
             assert S.int_diagonal == (int(c) if env == "0" and c <= 8 else 0)
-            for v in ("hs", "pr"):
+            for v in ("hs", "pr", "pipe_pr"):
                 for k in (1, 5, 20):
                     res = S.solve(b, variant=v, tol=0.0, maxit=k, history=True)
                     assert res.iters == k
-                    assert _fixed_sweeps(S) == (k - 1 if v == "hs" else k)
+                    assert _fixed_sweeps(S) == _want_fixed(v, k)
                     xs[(env, v, k)] = (res.x.cpu().numpy(), res.hist)
-    for v in ("hs", "pr"):
+    for v in ("hs", "pr", "pipe_pr"):
         band = OracleBand(v, A, prob.b, d, 20)
         for k in (1, 5, 20):
             xi, hi = xs[("0", v, k)]
