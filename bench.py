@@ -89,14 +89,15 @@ def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int, dvec=Non
     inner-product term, one multiply per use of an explicit M^{-1} v).  A
     constant-coefficient stencil row counts 1: its neighbour sum is formed in
     fixed point on the integer pipes, leaving the FMA c p_i - sum; with
-    `int_row` (an integer diagonal) the single-product sweeps form the whole
-    row in integers and it counts 0.  Integer work is not counted.
+    `int_row` (an integer diagonal) the product sweeps form their rows from
+    block fixed-point copies in integers and it counts 0.  Integer work and
+    the copies' bytes are not counted (the bytes are the algorithm's).
     """
     V = 8.0 * n
     A = 12.0 * nnz + 4.0 * (n + 1) if op == "csr" else 0.0
     m = float(nnz) if op == "csr" else 1.0 * n
-    # an integer stencil diagonal: the single-product sweeps (which read the
-    # block fixed-point copy of p) form the row without an FP64 instruction
+    # an integer stencil diagonal: the product sweeps, which read block
+    # fixed-point copies, form their rows without an FP64 instruction
     m1 = 0.0 if (int_row and op == "stencil") else m
     if dvec is None:
         dvec = precond == "jacobi" and op == "csr"
@@ -115,8 +116,8 @@ def sweep_models(variant: str, op: str, precond: str, n: int, nnz: int, dvec=Non
         return [("k_pr_a", 7 * V, 4 * n), ("k_pr_b", 3 * V + A, m1 + 3 * n)]
     if variant in ("pipe_pr", "pipe_m"):
         if jac:
-            return [("k_pipe", (12 + dv) * V + A, 2 * m + 13 * n)]
-        return [("k_pipe", 8 * V + A, 2 * m + 9 * n)]
+            return [("k_pipe", (12 + dv) * V + A, 2 * m1 + 13 * n)]
+        return [("k_pipe", 8 * V + A, 2 * m1 + 9 * n)]
     raise KeyError(variant)
 
 
