@@ -126,10 +126,10 @@ int prcg_create_csr(prcg_ctx** out, int64_t n, int64_t nnz,
  * in 64-bit fixed point and rounded once (see prcg_test_neighbour_sum), then
  * one FP64 FMA; it differs from an FP64 evaluation in the order of the
  * stencil only in rounding, and is the more accurate of the two.  On the
- * graph path of HS-CG, PR-CG and M-CG the product sweep adds the neighbours
- * from a block fixed-point copy of p instead (prcg_last_fixed_sweeps), and
- * with an integer diagonal in [1, 8] it forms the whole row in integers
- * (prcg_int_diagonal).  The variable-coefficient product is an FP64 FMA
+ * graph path of HS-CG, PR-CG, M-CG and the pipelined variants the product
+ * sweeps add the neighbours from block fixed-point copies of the vectors
+ * instead (prcg_last_fixed_sweeps), and with an integer diagonal in [1, 8]
+ * form the whole row in integers (prcg_int_diagonal).  The variable-coefficient product is an FP64 FMA
  * per entry.
  */
 int prcg_create_stencil(prcg_ctx** out, int dim, int64_t nx, int64_t ny, int64_t nz,
@@ -284,8 +284,11 @@ int prcg_last_launches(const prcg_ctx* ctx, int64_t* kernels);
  * rounding: a normwise bound, below 2^-58 max |p| per term, instead of the
  * per-row bound of the fixed-point sum of the other sweeps.  A value
  * outside its window (never expected) makes that sweep use the per-row
- * sums; PRCG_NO_FIXED_P=1 disables the copy.  0 for the persistent path and
- * for other operators and variants.
+ * sums; PRCG_NO_FIXED_P=1 disables the copy.  pipe-PR-CG and pipe-M-CG do
+ * the same with copies of r~ and s~ (stored by each sweep, read from the
+ * third sweep on) for both of their products; their count is of the sweeps
+ * that read them.  0 for the persistent path, the no-recompute ablations
+ * and other operators and variants.
  */
 int prcg_last_fixed_sweeps(const prcg_ctx* ctx, int64_t* sweeps);
 
@@ -300,8 +303,8 @@ int prcg_jacobi_form(const prcg_ctx* ctx);
 /*
  * prcg_int_diagonal -- the diagonal c of a constant-coefficient stencil
  * context when it is an integer in [1, 8] (2*dim plus an integer shift, e.g.
- * Poisson: 4 in 2D, 6 in 3D), with which the product sweeps that read the
- * block fixed-point copy of p form each row c P_i - sum_j P_j exactly in
+ * Poisson: 4 in 2D, 6 in 3D), with which the product sweeps that read a
+ * block fixed-point copy P form each row c P_i - sum_j P_j exactly in
  * 64-bit integers and round it once (no FP64 instruction; the error is that
  * of the copy, normwise, see prcg_last_fixed_sweeps).  0 when the diagonal
  * is not such an integer, the operator is not a constant stencil, or
