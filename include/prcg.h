@@ -246,9 +246,11 @@ int prcg_last_timing(const prcg_ctx* ctx, float* init_ms, float* loop_ms, int* i
 /*
  * prcg_time_sweeps -- average device time of each sweep (kernel) of one
  * iteration of `variant`, from CUDA events recorded around every launch on
- * the context's stream.  Runs initialize() and then `reps` iterations for a
- * fixed right-hand side without structure (b_i in [0.5, 1.5), a hash of i)
- * and x_0 = 0, with the stopping and breakdown tests switched off (the
+ * the context's stream.  Runs initialize(), two untimed iterations (after
+ * which every sweep is in the form it takes for the rest of a solve) and
+ * then `reps` timed iterations for a fixed right-hand side without
+ * structure (b_i in [0.5, 1.5), a hash of i) and x_0 = 0, with the stopping
+ * and breakdown tests switched off (the
  * sweeps always do their full work), and leaves the context's vectors in an
  * unspecified state (the next prcg_solve copies its own b and x_0 in).
  *   ms_per_sweep  float[3]: HS: sweeps A (x, r), B (p), C (s = A p);
